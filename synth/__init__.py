@@ -1,0 +1,121 @@
+"""Seeded synthetic compressed-sensing instances (measurement model only).
+
+This module draws the inputs that both the FP64 oracle and the CUDA path
+consume: the row set Omega, the sparse signal x and the measurement
+y = Phi x + eta of the problem statement (Sec. I, Eq. CSbasic).  It holds no
+part of the recovery method: no correlation, no transform, no least squares.
+The entries Phi(m, k) = A(Omega_m, k) it needs are evaluated from their closed
+forms one column at a time (Sec. I: Phi = S_Omega A):
+
+* WHT (Sylvester):  A(i, k) = (-1)^popcount(i & k) / sqrt(N)
+* DFT:              A(i, k) = exp(-2 pi i * (i k mod N) / N) / sqrt(N)
+
+Generation recipe (the paper fixes none of it; these are the stated readings):
+Omega is drawn uniformly without replacement and sorted ascending; the support
+is K distinct indices drawn uniformly; nonzeros are N(0,1) (real), CN(0,1)
+(complex, re/im each N(0,1/2)) or Rademacher +-1; noise is added per instance
+at the requested SNR, sigma^2 = ||Phi x||^2 / (M 10^(SNR/10)).  All draws use
+numpy's PCG64 ``default_rng(seed)``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+WHT = "wht"
+DFT = "dft"
+
+
+def draw_omega(N: int, M: int, rng: np.random.Generator) -> np.ndarray:
+    """M distinct row indices in [0, N), sorted ascending (int32)."""
+    if not (0 <= M <= N):
+        raise ValueError("need 0 <= M <= N")
+    return np.sort(rng.choice(N, size=M, replace=False)).astype(np.int32)
+
+
+def draw_support(N: int, K: int, rng: np.random.Generator) -> np.ndarray:
+    """K distinct column indices in [0, N) in drawn order (int32)."""
+    return rng.choice(N, size=K, replace=False).astype(np.int32)
+
+
+def draw_values(K: int, kind: str, dist: str, rng: np.random.Generator) -> np.ndarray:
+    """Nonzero values: 'gauss' (N(0,1) or CN(0,1)) or 'rademacher' (+-1)."""
+    if dist == "gauss":
+        if kind == DFT:
+            return (rng.standard_normal(K) + 1j * rng.standard_normal(K)) / np.sqrt(2.0)
+        return rng.standard_normal(K)
+    if dist == "rademacher":
+        s = rng.integers(0, 2, size=K) * 2.0 - 1.0
+        return s.astype(np.complex128) if kind == DFT else s
+    raise ValueError(f"unknown value distribution {dist!r}")
+
+
+def sensing_column(kind: str, N: int, omega: np.ndarray, k: int) -> np.ndarray:
+    """Column k of Phi = S_Omega A, from the closed form of A (FP64)."""
+    om = omega.astype(np.int64)
+    if kind == WHT:
+        par = np.bitwise_count(om & np.int64(k)) & 1
+        return (1.0 - 2.0 * par) / np.sqrt(N)
+    ph = (om * np.int64(k)) % N
+    return np.exp(-2j * np.pi * ph / N) / np.sqrt(N)
+
+
+def measure(kind: str, N: int, omega: np.ndarray, support: np.ndarray, values: np.ndarray) -> np.ndarray:
+    """Noiseless y = Phi x for x supported on ``support`` (FP64 / complex128)."""
+    y = np.zeros(len(omega), dtype=np.complex128 if kind == DFT else np.float64)
+    for k, v in zip(support.tolist(), values.tolist()):
+        y += v * sensing_column(kind, N, omega, k)
+    return y
+
+
+def add_noise(y: np.ndarray, snr_db: float | None, rng: np.random.Generator) -> np.ndarray:
+    if snr_db is None:
+        return y
+    M = len(y)
+    sigma2 = float(np.vdot(y, y).real) / (M * 10.0 ** (snr_db / 10.0))
+    if np.iscomplexobj(y):
+        eta = (rng.standard_normal(M) + 1j * rng.standard_normal(M)) * np.sqrt(sigma2 / 2.0)
+    else:
+        eta = rng.standard_normal(M) * np.sqrt(sigma2)
+    return y + eta
+
+
+def working_dtype(kind: str, prec: str):
+    """numpy dtype of y / h in the given precision ('fp64' or 'fp32')."""
+    if kind == DFT:
+        return np.complex128 if prec == "fp64" else np.complex64
+    return np.float64 if prec == "fp64" else np.float32
+
+
+def make_batch(kind: str, N: int, M: int, K: int, B: int, *, snr_db=None, dist="gauss",
+               prec="fp32", seed: int = 0, omega_seed: int | None = None) -> dict:
+    """B instances sharing one Omega.
+
+    Omega comes from ``default_rng(omega_seed)`` (``seed`` if None); instance b
+    draws its support, values and noise from ``default_rng(seed + 1 + b)``.
+    ``Y`` is stored in the working precision (rounded once); the oracle and
+    the GPU both read that rounded array.
+    """
+    rng0 = np.random.default_rng(seed if omega_seed is None else omega_seed)
+    omega = draw_omega(N, M, rng0)
+    supports, values, ys = [], [], []
+    for b in range(B):
+        rng = np.random.default_rng(seed + 1 + b)
+        s = draw_support(N, K, rng)
+        v = draw_values(K, kind, dist, rng)
+        y = add_noise(measure(kind, N, omega, s, v), snr_db, rng)
+        supports.append(s)
+        values.append(v)
+        ys.append(y)
+    dt = working_dtype(kind, prec)
+    return {
+        "kind": kind, "N": N, "M": M, "K": K, "B": B, "prec": prec,
+        "omega": omega,
+        "support": np.stack(supports) if B else np.zeros((0, K), np.int32),
+        "values": np.stack(values) if B else np.zeros((0, K)),
+        "Y": (np.stack(ys) if B else np.zeros((0, M))).astype(dt),
+    }
+
+
+# Workloads used by the tests and the benchmark (sizes, not data).
+CONFIG_WHT_FP64_SINGLE = dict(kind=WHT, N=1024, M=256, K=16, B=1, snr_db=None, prec="fp64", seed=0)
+CONFIG_DFT_C64_BATCH = dict(kind=DFT, N=4096, M=1024, K=64, B=1024, snr_db=40.0, prec="fp32", seed=0)

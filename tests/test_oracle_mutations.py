@@ -1,0 +1,79 @@
+"""Plants plausible slips in the oracle (on the CPU, through monkeypatch) and
+checks that the pins of test_oracle_pins.py catch each one.  Nothing here
+touches a GPU."""
+import numpy as np
+import pytest
+
+import tests.test_oracle_pins as pins
+from oracle import kernelsum, matrices, omp
+
+
+def caught(fn, *a, **k):
+    with pytest.raises(AssertionError):
+        fn(*a, **k)
+
+
+def test_wrong_dft_sign_is_caught(monkeypatch):
+    def bad_fourier(N):
+        i = np.arange(N)
+        return np.exp(+2j * np.pi * (np.outer(i, i) % N) / N) / np.sqrt(N)
+    monkeypatch.setattr(matrices, "fourier", bad_fourier)
+    caught(pins.test_fourier_matches_fft, 8)
+
+
+def test_missing_normalisation_is_caught(monkeypatch):
+    orig = matrices.hadamard
+    monkeypatch.setattr(matrices, "hadamard", lambda N: orig(N) * np.sqrt(N))
+    caught(pins.test_unitary_and_unimodular, "wht", 8)
+
+
+def test_dropped_conjugate_is_caught(monkeypatch):
+    monkeypatch.setattr(omp, "correlate", lambda Phi, r: Phi.T @ r)
+    caught(pins.test_correlation_is_adjoint, "dft")
+
+
+def test_reversed_shift_is_caught(monkeypatch):
+    def bad_shift(kind, N, j, lam):
+        j = np.asarray(j, dtype=np.int64)
+        return (lam - j) % N if kind == "dft" else j ^ lam
+    monkeypatch.setattr(kernelsum, "shift_index", bad_shift)
+    caught(pins.test_gram_is_shifted_kernel, "dft")
+    caught(pins.test_fast_equals_conventional, "dft")
+
+
+def test_transposed_kernel_definition_is_caught(monkeypatch):
+    def bad_kernel(kind, N, omega):
+        U = matrices.unitary(kind, N)
+        S = matrices.row_selector(N, omega)
+        e0 = np.zeros(N)
+        e0[0] = 1
+        return U @ (S.T @ (S @ (U.conj().T @ e0)))   # U and U^H swapped
+    monkeypatch.setattr(kernelsum, "kernel_vector", bad_kernel)
+    caught(pins.test_gram_is_shifted_kernel, "dft")
+
+
+def test_highest_index_tie_break_is_caught(monkeypatch):
+    def bad_identify(h, excluded):
+        score = (np.conj(h) * h).real.astype(float).copy()
+        if len(excluded):
+            score[np.asarray(excluded)] = -np.inf
+        j = len(score) - 1 - int(np.argmax(score[::-1]))
+        return j, 1.0
+    monkeypatch.setattr(omp, "identify", bad_identify)
+    caught(pins.test_tiny_omp_by_hand)
+
+
+def test_transposed_gram_in_least_squares_is_caught(monkeypatch):
+    def bad_ls(Phi_t, y):
+        G = Phi_t.T @ Phi_t          # missing conjugate
+        b = Phi_t.conj().T @ y
+        return np.linalg.solve(G, b), 1.0
+    monkeypatch.setattr(omp, "least_squares", bad_ls)
+    caught(pins.test_omp_invariants, "dft")
+
+
+def test_dropped_kernel_term_is_caught(monkeypatch):
+    orig = kernelsum.fast_correlation_dense
+    bad_fast_impl = lambda kind, N, c, h0, support, x: orig(kind, N, c, h0, support[:-1], x[:-1])
+    monkeypatch.setattr(kernelsum, "fast_correlation_dense", bad_fast_impl)
+    caught(pins.test_fast_equals_conventional, "wht")
