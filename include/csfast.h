@@ -1,0 +1,146 @@
+/*
+ * csfast — fast correlation for matching pursuit on GB300 (sm_103a).
+ *
+ * C ABI of libcsfast.so.  The library implements, for partial unitary sensing
+ * matrices Phi = S_Omega A with A the unitary Walsh–Hadamard (Sylvester,
+ * A(i,k) = (-1)^popcount(i&k)/sqrt(N)) or DFT (A(i,k) = exp(-2 pi i ik/N)/sqrt(N))
+ * matrix (Sec. I of Kim et al., arXiv 1205.4139):
+ *
+ *   - the correlation kernel vector c = U^H S^T S U e_1      (Eq. kernelsum)
+ *   - the conventional correlation h = Phi^H r              (Algorithm 1.1, step 2)
+ *   - the fast correlation h = h_0 - sum x(t) P_{lambda_t} c (Eq. kernelsumOMP)
+ *   - OMP (Algorithm 1.1) with either correlation, or the adaptive switch of
+ *     Sec. IV, and an FP64 least-squares update whose Gram entries are read
+ *     off c.
+ *
+ * Conventions for every entry point:
+ *   - Indices are 0-based.  N is a power of two.  Omega is sorted ascending,
+ *     duplicate-free, with entries in [0, N).
+ *   - Element type F of r, y, h, h_0 and the correlation-side x follows the
+ *     plan's (kind, prec):  WHT+FP64 double, WHT+FP32 float,
+ *     DFT+FP64 double2 (re, im interleaved), DFT+FP32 float2.
+ *     OMP coefficients (x_dev of cs_omp) are always FP64: double for WHT,
+ *     interleaved complex double for DFT.
+ *   - Pointers named *_dev are device pointers owned by the caller; they must
+ *     stay valid until the work queued on `stream` has completed.  `stream`
+ *     is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream unless stated otherwise.
+ *   - Batched arrays are dense row-major: instance b of an F[n] array starts
+ *     at element b*n.
+ *   - A plan owns its device tables and a workspace that grows on demand.
+ *     Calls that use the same plan must not overlap in time (queue them on
+ *     one stream); different plans are independent.
+ *   - Errors: argument problems are reported synchronously as CS_ERR_INVALID
+ *     before anything is queued; sizes beyond the kernels' limits give
+ *     CS_ERR_UNSUPPORTED; a failing CUDA call gives CS_ERR_CUDA (text via
+ *     cs_last_error).  The library never aborts the process.
+ */
+#ifndef CSFAST_H
+#define CSFAST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_plan_s* cs_plan_t;
+
+typedef enum {
+  CS_OK = 0,
+  CS_ERR_INVALID = 1,
+  CS_ERR_NOMEM = 2,
+  CS_ERR_CUDA = 3,
+  CS_ERR_UNSUPPORTED = 4
+} cs_status;
+
+typedef enum { CS_WHT = 0, CS_DFT = 1 } cs_kind;
+typedef enum { CS_FP64 = 0, CS_FP32 = 1 } cs_prec;
+
+/* Which correlation OMP uses at iteration t (t = 1 is always one transform,
+ * Eq. kernelsumOMP):  FAST = kernel sums for every t > 1;  CONV = a transform
+ * of the zero-filled residual at every t (Algorithm 1.1 step 2);  HYBRID =
+ * kernel sums while t <= t_switch, transforms after (the adaptive strategy of
+ * Sec. IV). */
+typedef enum { CS_PATH_FAST = 0, CS_PATH_CONV = 1, CS_PATH_HYBRID = 2 } cs_path;
+
+/* Halting rule of Algorithm 1.1 step 8 (the paper leaves it open): stop after
+ * K iterations, or as soon as ||r_t|| < rel_tol * ||y|| (rel_tol = 0 disables
+ * the tolerance).  A zero measurement halts before the first iteration; a
+ * selected column whose Cholesky pivot is <= 1e-10 * M/N (numerically
+ * dependent on the support) ends the run without being added.
+ * t_switch < 0 selects the plan's default switch point (cs_plan_info). */
+typedef struct {
+  double rel_tol;
+  int32_t path;
+  int32_t t_switch;
+} cs_halt;
+
+/* Build a plan for Phi = S_Omega A (Sec. I).  Computes on the device the
+ * correlation kernel vector c = U^H S^T S U e_1 of Eq. (kernelsum) in FP64
+ * (and rounded to FP32 for FP32 plans), the transform twiddles and the index
+ * maps of Omega.  `omega_host` is a host array of M int32 (M may be 0).
+ * Blocks until the plan's tables are built.  Limits: 1 <= N <= 8192 (whole
+ * instance on one SM), 0 <= M <= N. */
+cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind,
+                         int32_t prec, void* stream, cs_plan_t* out);
+
+/* Release the plan's device memory (synchronises the device first). */
+cs_status cs_plan_destroy(cs_plan_t plan);
+
+/* Report the plan's sizes and its default hybrid switch point: the largest t
+ * whose kernel-sum cost is no more than one transform's in the flop model of
+ * Table I (Sec. IV's "excessive point"), unless the library was tuned for
+ * this (kind, prec, N). Any output pointer may be NULL. */
+cs_status cs_plan_info(cs_plan_t plan, int64_t* N, int64_t* M, int32_t* kind, int32_t* prec,
+                       int32_t* t_switch_default);
+
+/* Copy the correlation kernel vector c (Eq. kernelsum) into c_dev:
+ * `prec` CS_FP64 gives double / double2 [N], CS_FP32 float / float2 [N]. */
+cs_status cs_plan_kernel(cs_plan_t plan, void* c_dev, int32_t prec, void* stream);
+
+/* Conventional correlation (Algorithm 1.1 step 2): for each of `batch`
+ * residuals r (F[M], entry m belongs to row Omega_m) computes
+ * h = Phi^H r = A^H zf_Omega(r) (F[N]) with one transform.  h_dev may be NULL
+ * when only the arg-max is wanted; argmax_dev (int32[batch], NULL allowed)
+ * receives argmax_j |h(j)|^2, lowest j on ties (step 3). */
+cs_status cs_correlate(cs_plan_t plan, const void* r_dev, int64_t batch, void* h_dev,
+                       int32_t* argmax_dev, void* stream);
+
+/* Fast correlation (Eq. kernelsum / kernelsumOMP):
+ *   h(j) = h_0(j) - sum_{k<s} x(k) c(j (-) supp(k)),
+ * (-) being (j - l) mod N for DFT and j XOR l for WHT.  Per instance:
+ * h0 F[N], supp int32[s] (distinct, in [0, N)), x F[s].  h_dev may be NULL;
+ * argmax_dev (NULL allowed) receives argmax over j not in supp of |h(j)|^2,
+ * lowest j on ties (-1 if every j is in supp). s may be 0 (h = h_0). */
+cs_status cs_correlate_fast(cs_plan_t plan, const void* h0_dev, const int32_t* supp_dev,
+                            const void* x_dev, int32_t s, int64_t batch, void* h_dev,
+                            int32_t* argmax_dev, void* stream);
+
+/* OMP (Algorithm 1.1) on `batch` measurements y (F[M] each) sharing the
+ * plan's Omega, one fused persistent kernel for the whole batch.  Outputs per
+ * instance b:
+ *   x_dev      FP64 coefficients [K] in selection order (double or
+ *              interleaved complex double), zero past iters
+ *   supp_dev   int32 [K] support in selection order, -1 past iters
+ *   iters_dev  int32: number of selected columns
+ *   resnorm_dev double: ||r|| / ||y|| at exit (0 for y = 0), from the FP64
+ *              downdate ||r_t||^2 = ||y||^2 - sum |z_k|^2 of the Cholesky
+ *              update
+ * Any output pointer except supp_dev may be NULL (supp_dev too when K = 0).  halt may be NULL
+ * (rel_tol 1e-6, hybrid path, default switch).  Limits: 0 <= K <= min(M, 1024). */
+cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
+                 void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev,
+                 void* stream);
+
+/* Short static description of a status code. */
+const char* cs_status_string(cs_status s);
+
+/* Thread-local text of the last CUDA error seen by this thread ("" if none). */
+const char* cs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSFAST_H */

@@ -30,6 +30,14 @@ def kernel_vector(kind: str, N: int, omega) -> np.ndarray:
     return U.conj().T @ (S.T @ (S @ (U @ e0)))
 
 
+def kernel_vector_rows(kind: str, N: int, omega) -> np.ndarray:
+    """c(j) = sum_{i in Omega} conj(U(i, j)) U(i, 0): Eq. (kernelsum) expanded
+    entry by entry over the rows of Phi, for N too large for a dense U."""
+    from .matrices import sensing_rows
+    Phi = sensing_rows(kind, N, omega)
+    return Phi.conj().T @ Phi[:, 0] if len(Phi) else np.zeros(N)
+
+
 def permutation(kind: str, N: int, lam: int) -> np.ndarray:
     """P_lambda = U^H D_lambda U, D_lambda = sqrt(N) diag(u_lambda) (Theorem 2-1)."""
     U = unitary(kind, N)

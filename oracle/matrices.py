@@ -52,3 +52,15 @@ def row_selector(N: int, omega) -> np.ndarray:
 def sensing(kind: str, N: int, omega) -> np.ndarray:
     """Phi = S_Omega A (Sec. I), as a dense M x N array."""
     return row_selector(N, omega) @ unitary(kind, N)
+
+
+def sensing_rows(kind: str, N: int, omega) -> np.ndarray:
+    """Phi = S_Omega A built row by row from the entries of A, for N too large
+    to form A itself: A(i,k) = (-1)^popcount(i&k)/sqrt(N) (Sylvester; pinned
+    against the Kronecker construction in the tests) or
+    exp(-2 pi i (ik mod N)/N)/sqrt(N)."""
+    om = np.asarray(omega, dtype=np.int64)[:, None]
+    k = np.arange(N, dtype=np.int64)[None, :]
+    if kind == "wht":
+        return (1.0 - 2.0 * (np.bitwise_count(om & k) & 1)) / np.sqrt(N)
+    return np.exp(-2j * np.pi * ((om * k) % N) / N) / np.sqrt(N)

@@ -1,0 +1,179 @@
+"""ctypes binding of libcsfast.so (C ABI in include/csfast.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Tensors are torch CUDA tensors (torch supplies device memory and
+the current stream); complex tensors use torch's interleaved (re, im) layout,
+which is the library's.  The library is loaded on first use and a missing
+library raises ``RuntimeError``; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libcsfast.so")
+
+CS_WHT, CS_DFT = 0, 1
+CS_FP64, CS_FP32 = 0, 1
+PATHS = {"fast": 0, "conv": 1, "hybrid": 2}
+KINDS = {"wht": CS_WHT, "dft": CS_DFT}
+PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
+
+# Every function include/csfast.h declares.
+EXPORTS = ["cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_kernel", "cs_correlate",
+           "cs_correlate_fast", "cs_omp", "cs_status_string", "cs_last_error"]
+
+
+class CsError(RuntimeError):
+    pass
+
+
+class Halt(ctypes.Structure):
+    _fields_ = [("rel_tol", ctypes.c_double), ("path", ctypes.c_int32), ("t_switch", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library and declare the signatures (no GPU needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    pi32 = ctypes.POINTER(ctypes.c_int32)
+    pi64 = ctypes.POINTER(ctypes.c_int64)
+    L.cs_plan_create.argtypes = [i64, pi32, i64, i32, i32, vp, ctypes.POINTER(vp)]
+    L.cs_plan_destroy.argtypes = [vp]
+    L.cs_plan_info.argtypes = [vp, pi64, pi64, pi32, pi32, pi32]
+    L.cs_plan_kernel.argtypes = [vp, vp, i32, vp]
+    L.cs_correlate.argtypes = [vp, vp, i64, vp, vp, vp]
+    L.cs_correlate_fast.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, vp]
+    L.cs_omp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
+    for f in ("cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_kernel", "cs_correlate",
+              "cs_correlate_fast", "cs_omp"):
+        getattr(L, f).restype = ctypes.c_int
+    L.cs_status_string.argtypes = [ctypes.c_int]
+    L.cs_status_string.restype = ctypes.c_char_p
+    L.cs_last_error.argtypes = []
+    L.cs_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != 0:
+        L = load()
+        raise CsError(f"csfast status {st}: {L.cs_status_string(st).decode()} {L.cs_last_error().decode()}".strip())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def working_dtype(kind: str, prec: str):
+    import torch
+    if kind == "dft":
+        return torch.complex64 if prec == "fp32" else torch.complex128
+    return torch.float32 if prec == "fp32" else torch.float64
+
+
+def ls_dtype(kind: str):
+    import torch
+    return torch.complex128 if kind == "dft" else torch.float64
+
+
+class Plan:
+    """A plan for Phi = S_Omega A (cs_plan_create)."""
+
+    def __init__(self, N: int, omega, kind: str = "dft", prec: str = "fp32", stream=None):
+        L = load()
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.int32))
+        self.N, self.M, self.kind, self.prec = int(N), int(om.size), kind, prec
+        h = ctypes.c_void_p()
+        _check(L.cs_plan_create(self.N, om.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.M, KINDS[kind],
+                                PRECS[prec], _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.dtype = working_dtype(kind, prec)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().cs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        n, m = ctypes.c_int64(), ctypes.c_int64()
+        k, p, ts = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().cs_plan_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(k), ctypes.byref(p),
+                                   ctypes.byref(ts)))
+        return {"N": n.value, "M": m.value, "kind": k.value, "prec": p.value, "t_switch_default": ts.value}
+
+    def kernel_vector(self, prec: str = "fp64", stream=None):
+        import torch
+        c = torch.empty(self.N, dtype=working_dtype(self.kind, prec), device="cuda")
+        _check(load().cs_plan_kernel(self._h, _ptr(c), PRECS[prec], _stream(stream)))
+        return c
+
+    def _want(self, t, n_last):
+        if t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous() or t.shape[-1] != n_last:
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} tensor with last dim {n_last}")
+
+    def correlate(self, r, want_h: bool = True, stream=None):
+        """h = Phi^H r for a (batch, M) tensor; returns (h or None, argmax)."""
+        import torch
+        self._want(r, self.M)
+        B = r.shape[0]
+        h = torch.empty(B, self.N, dtype=self.dtype, device="cuda") if want_h else None
+        am = torch.empty(B, dtype=torch.int32, device="cuda")
+        _check(load().cs_correlate(self._h, _ptr(r), B, _ptr(h), _ptr(am), _stream(stream)))
+        return h, am
+
+    def correlate_fast(self, h0, supp, x, want_h: bool = True, stream=None):
+        """h = h0 - sum x(k) c(j (-) supp(k)) for (batch, N) h0, (batch, s) supp/x."""
+        import torch
+        self._want(h0, self.N)
+        B = h0.shape[0]
+        s = supp.shape[1] if supp.dim() == 2 else 0
+        if supp.dtype != torch.int32 or x.dtype != self.dtype or not supp.is_contiguous() or not x.is_contiguous():
+            raise ValueError("supp must be int32 and x of the plan's dtype, both contiguous")
+        h = torch.empty(B, self.N, dtype=self.dtype, device="cuda") if want_h else None
+        am = torch.empty(B, dtype=torch.int32, device="cuda")
+        _check(load().cs_correlate_fast(self._h, _ptr(h0), _ptr(supp) if s else None, _ptr(x) if s else None, s, B,
+                                        _ptr(h), _ptr(am), _stream(stream)))
+        return h, am
+
+    def omp_into(self, y, K: int, x, supp, iters, resnorm, rel_tol: float = 1e-6, path: str = "hybrid",
+                 t_switch: int = -1, stream=None):
+        """cs_omp into caller-provided outputs (no allocation)."""
+        hl = Halt(rel_tol, PATHS[path], t_switch)
+        _check(load().cs_omp(self._h, _ptr(y), y.shape[0], K, ctypes.byref(hl), _ptr(x), _ptr(supp), _ptr(iters),
+                             _ptr(resnorm), _stream(stream)))
+
+    def omp(self, y, K: int, rel_tol: float = 1e-6, path: str = "hybrid", t_switch: int = -1, stream=None):
+        """OMP on a (batch, M) tensor; returns x (FP64), supp, iters, resnorm."""
+        import torch
+        self._want(y, self.M)
+        B = y.shape[0]
+        x = torch.empty(B, K, dtype=ls_dtype(self.kind), device="cuda")
+        supp = torch.empty(B, K, dtype=torch.int32, device="cuda")
+        iters = torch.empty(B, dtype=torch.int32, device="cuda")
+        res = torch.empty(B, dtype=torch.float64, device="cuda")
+        self.omp_into(y, K, x, supp, iters, res, rel_tol, path, t_switch, stream)
+        return x, supp, iters, res

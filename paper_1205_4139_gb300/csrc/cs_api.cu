@@ -1,0 +1,241 @@
+// C ABI of libcsfast.so (declared in include/csfast.h): argument checks,
+// plan tables, workspace management and launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/csfast.h"
+#include "cs_internal.h"
+#include "cs_transform.cuh"
+
+using namespace csf;
+
+struct cs_plan_s {
+  PlanView v;
+  int kind, prec;
+  int device;
+  int t_switch_default;
+  int* d_slot = nullptr;
+  void* d_tw64 = nullptr;
+  void* d_tw32 = nullptr;
+  void* d_c64 = nullptr;
+  void* d_c32 = nullptr;
+  void* ws = nullptr;       // OMP workspace (grows on demand, stream-ordered)
+  size_t ws_bytes = 0;
+};
+
+static thread_local char g_err[256] = "";
+
+static cs_status cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? CS_ERR_NOMEM : CS_ERR_CUDA;
+}
+
+#define CS_CUDA(call, what)                       \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+static size_t elem_bytes(int kind, int prec) { return (kind == CS_DFT ? 2 : 1) * (prec == CS_FP32 ? 4 : 8); }
+
+extern "C" const char* cs_status_string(cs_status s) {
+  switch (s) {
+    case CS_OK: return "ok";
+    case CS_ERR_INVALID: return "invalid argument";
+    case CS_ERR_NOMEM: return "device allocation failed";
+    case CS_ERR_CUDA: return "CUDA error";
+    case CS_ERR_UNSUPPORTED: return "size beyond the kernels' limits";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* cs_last_error(void) { return g_err; }
+
+static void plan_free(cs_plan_s* p) {
+  if (!p) return;
+  cudaFree(p->d_slot);
+  cudaFree(p->d_tw64);
+  cudaFree(p->d_tw32);
+  cudaFree(p->d_c64);
+  cudaFree(p->d_c32);
+  cudaFree(p->ws);
+  delete p;
+}
+
+extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
+                                    void* stream, cs_plan_t* out) {
+  if (!out) return CS_ERR_INVALID;
+  *out = nullptr;
+  if (kind != CS_WHT && kind != CS_DFT) return CS_ERR_INVALID;
+  if (prec != CS_FP64 && prec != CS_FP32) return CS_ERR_INVALID;
+  if (N < 1 || (N & (N - 1))) return CS_ERR_INVALID;
+  if (M < 0 || M > N) return CS_ERR_INVALID;
+  if (M > 0 && !omega_host) return CS_ERR_INVALID;
+  for (int64_t m = 0; m < M; ++m) {
+    if (omega_host[m] < 0 || omega_host[m] >= N) return CS_ERR_INVALID;
+    if (m > 0 && omega_host[m] <= omega_host[m - 1]) return CS_ERR_INVALID;
+  }
+  int logN = 0;
+  while ((int64_t(1) << logN) < N) ++logN;
+  if (logN > kMaxLogN) return CS_ERR_UNSUPPORTED;
+
+  cs_plan_s* p = new (std::nothrow) cs_plan_s();
+  if (!p) return CS_ERR_NOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  p->kind = kind;
+  p->prec = prec;
+  cudaGetDevice(&p->device);
+  p->v.N = (int)N;
+  p->v.logN = logN;
+  p->v.M = (int)M;
+  p->v.dft = kind == CS_DFT;
+  p->v.fp32 = prec == CS_FP32;
+  // Sec. IV excessive point under the Table I flop model
+  p->t_switch_default = kind == CS_DFT ? 1 + (5 * logN) / 6 : 1 + logN;
+
+  // slot map: position -> m.  DFT positions are those of the forward DIF
+  // chain (the adjoint chain's input order); WHT positions are natural.
+  std::vector<int32_t> slot((size_t)N, -1);
+  for (int64_t m = 0; m < M; ++m) {
+    const int pos = kind == CS_DFT ? dif_position(omega_host[m], logN) : omega_host[m];
+    slot[(size_t)pos] = (int32_t)m;
+  }
+  const size_t wb = kind == CS_DFT ? 16 : 8;
+  cudaError_t e;
+#define PLAN_TRY(call, what)                    \
+  do {                                          \
+    e = (call);                                 \
+    if (e != cudaSuccess) {                     \
+      cs_status s_ = cuda_fail(e, what);        \
+      plan_free(p);                             \
+      return s_;                                \
+    }                                           \
+  } while (0)
+  PLAN_TRY(cudaMalloc(&p->d_slot, (size_t)N * sizeof(int32_t)), "cudaMalloc slot");
+  PLAN_TRY(cudaMemcpyAsync(p->d_slot, slot.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, st),
+           "copy slot");
+  if (kind == CS_DFT) {
+    PLAN_TRY(cudaMalloc(&p->d_tw64, (size_t)N * sizeof(double2)), "cudaMalloc twiddles");
+    if (prec == CS_FP32) PLAN_TRY(cudaMalloc(&p->d_tw32, (size_t)N * sizeof(float2)), "cudaMalloc twiddles");
+  }
+  PLAN_TRY(cudaMalloc(&p->d_c64, (size_t)N * wb), "cudaMalloc c");
+  if (prec == CS_FP32) PLAN_TRY(cudaMalloc(&p->d_c32, (size_t)N * wb / 2), "cudaMalloc c");
+  p->v.slot = p->d_slot;
+  p->v.tw64 = p->d_tw64;
+  p->v.tw32 = p->d_tw32;
+  p->v.c64 = p->d_c64;
+  p->v.c32 = p->d_c32;
+  if (kind == CS_DFT) PLAN_TRY(launch_twiddles(p->v, p->d_tw64, p->d_tw32, st), "twiddle kernel");
+  PLAN_TRY(launch_kernel_vector(p->v, p->d_c64, p->d_c32, st), "kernel-vector kernel");
+  PLAN_TRY(cudaStreamSynchronize(st), "plan synchronize");
+#undef PLAN_TRY
+  *out = p;
+  return CS_OK;
+}
+
+extern "C" cs_status cs_plan_destroy(cs_plan_t plan) {
+  if (!plan) return CS_ERR_INVALID;
+  cudaDeviceSynchronize();
+  plan_free(plan);
+  return CS_OK;
+}
+
+extern "C" cs_status cs_plan_info(cs_plan_t plan, int64_t* N, int64_t* M, int32_t* kind, int32_t* prec,
+                                  int32_t* t_switch_default) {
+  if (!plan) return CS_ERR_INVALID;
+  if (N) *N = plan->v.N;
+  if (M) *M = plan->v.M;
+  if (kind) *kind = plan->kind;
+  if (prec) *prec = plan->prec;
+  if (t_switch_default) *t_switch_default = plan->t_switch_default;
+  return CS_OK;
+}
+
+extern "C" cs_status cs_plan_kernel(cs_plan_t plan, void* c_dev, int32_t prec, void* stream) {
+  if (!plan || !c_dev) return CS_ERR_INVALID;
+  if (prec != CS_FP64 && prec != CS_FP32) return CS_ERR_INVALID;
+  const size_t n = (size_t)plan->v.N;
+  if (prec == CS_FP64) {
+    CS_CUDA(cudaMemcpyAsync(c_dev, plan->d_c64, n * elem_bytes(plan->kind, CS_FP64), cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream),
+            "copy c");
+    return CS_OK;
+  }
+  if (plan->d_c32) {
+    CS_CUDA(cudaMemcpyAsync(c_dev, plan->d_c32, n * elem_bytes(plan->kind, CS_FP32), cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream),
+            "copy c");
+    return CS_OK;
+  }
+  // FP64 plan asked for FP32 c: round through a temporary plan view
+  PlanView v = plan->v;
+  v.fp32 = true;
+  CS_CUDA(launch_kernel_vector(v, plan->d_c64, c_dev, (cudaStream_t)stream), "round c");
+  return CS_OK;
+}
+
+extern "C" cs_status cs_correlate(cs_plan_t plan, const void* r_dev, int64_t batch, void* h_dev, int32_t* argmax_dev,
+                                  void* stream) {
+  if (!plan || batch < 0) return CS_ERR_INVALID;
+  if (batch > 0 && plan->v.M > 0 && !r_dev) return CS_ERR_INVALID;
+  if (batch == 0 || (!h_dev && !argmax_dev)) return CS_OK;
+  CS_CUDA(launch_correlate(plan->v, r_dev, batch, h_dev, argmax_dev, (cudaStream_t)stream), "correlate");
+  return CS_OK;
+}
+
+extern "C" cs_status cs_correlate_fast(cs_plan_t plan, const void* h0_dev, const int32_t* supp_dev,
+                                       const void* x_dev, int32_t s, int64_t batch, void* h_dev, int32_t* argmax_dev,
+                                       void* stream) {
+  if (!plan || batch < 0 || s < 0 || s > plan->v.N) return CS_ERR_INVALID;
+  if (batch > 0 && !h0_dev) return CS_ERR_INVALID;
+  if (batch > 0 && s > 0 && (!supp_dev || !x_dev)) return CS_ERR_INVALID;
+  if (s > kMaxK) return CS_ERR_UNSUPPORTED;
+  if (batch == 0 || (!h_dev && !argmax_dev)) return CS_OK;
+  CS_CUDA(launch_correlate_fast(plan->v, h0_dev, supp_dev, x_dev, s, batch, h_dev, argmax_dev, (cudaStream_t)stream),
+          "correlate_fast");
+  return CS_OK;
+}
+
+extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
+                            void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev, void* stream) {
+  if (!plan || batch < 0 || K < 0) return CS_ERR_INVALID;
+  if (K > plan->v.M) return CS_ERR_INVALID;
+  if (K > kMaxK) return CS_ERR_UNSUPPORTED;
+  cs_halt h = {1e-6, CS_PATH_HYBRID, -1};
+  if (halt) h = *halt;
+  if (!(h.rel_tol >= 0.0) || !std::isfinite(h.rel_tol)) return CS_ERR_INVALID;
+  if (h.path != CS_PATH_FAST && h.path != CS_PATH_CONV && h.path != CS_PATH_HYBRID) return CS_ERR_INVALID;
+  if (batch == 0) return CS_OK;
+  if (K > 0 && !supp_dev) return CS_ERR_INVALID;
+  if (plan->v.M > 0 && !y_dev) return CS_ERR_INVALID;
+  const int t_switch = h.t_switch < 0 ? plan->t_switch_default : h.t_switch;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  int err = 0;
+  const int grid = omp_grid(plan->v, K, h.path, batch, &err);
+  if (err) return cuda_fail((cudaError_t)err, "omp configuration");
+  const size_t need = omp_workspace_bytes(plan->v, K, grid);
+  if (need > plan->ws_bytes) {
+    if (plan->ws) CS_CUDA(cudaFreeAsync(plan->ws, st), "cudaFreeAsync workspace");
+    plan->ws = nullptr;
+    plan->ws_bytes = 0;
+    CS_CUDA(cudaMallocAsync(&plan->ws, need, st), "cudaMallocAsync workspace");
+    plan->ws_bytes = need;
+  }
+  OmpLaunch a;
+  a.y = y_dev;
+  a.batch = batch;
+  a.K = K;
+  a.rel_tol = h.rel_tol;
+  a.path = h.path;
+  a.t_switch = t_switch;
+  a.x_out = x_dev;
+  a.supp_out = supp_dev;
+  a.iters_out = iters_dev;
+  a.res_out = resnorm_dev;
+  CS_CUDA(launch_omp(plan->v, a, plan->ws, grid, st), "omp kernel");
+  return CS_OK;
+}

@@ -1,0 +1,298 @@
+// Block-level building blocks of the hot path, each run by one CTA on one
+// instance:
+//   * correlate_transform  h = A^H zf_Omega(v)         (Algorithm 1.1 step 2)
+//   * correlate_residual   h = A^H zf(y - S A x_Lambda) (steps 7 and 2)
+//   * correlate_fast       h = h_0 - sum_k x_k c(j (-) lambda_k)
+//                                                      (Eq. kernelsumOMP)
+//   * each followed by the identification of step 3 (arg-max of |h|^2 over j
+//     not in Lambda, lowest j on ties)
+//   * ls_append            the FP64 least-squares update of step 6 for one
+//     new column, with the Gram column read off c (Eq. kernelsum).
+#pragma once
+#include "cs_transform.cuh"
+
+namespace csf {
+
+// Static per-plan data every kernel reads.
+template <class E>
+struct PlanDev {
+  int N, logN, M;
+  const int* __restrict__ slot;  // [N]: m if position holds row Omega_m, else -1
+  const E* __restrict__ tw;      // DIF twiddles in the working precision (DFT only)
+  const E* __restrict__ c;       // correlation kernel vector, working precision [N]
+  const typename FT<E>::W* __restrict__ c64;  // correlation kernel vector, FP64 [N]
+};
+
+// |h|^2 type used for identification: the working precision.
+template <class E> struct NormT { using V = typename FT<E>::R; };
+
+// Unnormalised transform of the kind: DFT uses F^H (adjoint chain) for the
+// correlation and F (forward chain) for the synthesis; WHT uses H for both.
+template <class E, bool DFT>
+__device__ __forceinline__ void transform_adjoint(E* buf, const PlanDev<E>& P) {
+  if constexpr (DFT) dft_adjoint(buf, P.logN, P.tw);
+  else wht(buf, P.logN);
+}
+template <class E, bool DFT>
+__device__ __forceinline__ void transform_forward(E* buf, const PlanDev<E>& P) {
+  if constexpr (DFT) dft_forward(buf, P.logN, P.tw);
+  else wht(buf, P.logN);
+}
+
+__device__ __forceinline__ bool in_bits(const uint32_t* bits, int j) { return (bits[j >> 5] >> (j & 31)) & 1u; }
+
+// Arg-max of |buf(j)|^2 over j not flagged in `bits` (NULL: no exclusions);
+// optionally writes buf to h_out in natural order.
+template <class E>
+__device__ int argmax_buffer(const E* buf, int N, const uint32_t* bits, E* __restrict__ h_out,
+                             typename NormT<E>::V* rv, int* rj) {
+  using V = typename NormT<E>::V;
+  V bv = (V)-1;
+  int bj = 0x7fffffff;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const E h = buf[swz<E>(j)];
+    if (h_out) h_out[j] = h;
+    const V v = (bits && in_bits(bits, j)) ? (V)-1 : (V)norm2(h);
+    if (better(v, j, bv, bj)) { bv = v; bj = j; }
+  }
+  return block_argmax(bv, bj, rv, rj);
+}
+
+// buf <- scale * zf_Omega(v) in the position order the adjoint chain expects;
+// returns sum |v_m|^2 over this thread's entries (FP64).
+template <class E>
+__device__ double load_zero_filled(E* buf, const PlanDev<E>& P, const E* __restrict__ v,
+                                   typename FT<E>::R scl) {
+  double s = 0.0;
+  for (int pos = threadIdx.x; pos < P.N; pos += blockDim.x) {
+    const int m = __ldg(P.slot + pos);
+    E e = zero<E>();
+    if (m >= 0) {
+      const E vm = v[m];
+      s += norm2(to_w(vm));
+      e = scale(vm, scl);
+    }
+    buf[swz<E>(pos)] = e;
+  }
+  __syncthreads();
+  return s;
+}
+
+// h = A^H zf_Omega(v): one adjoint transform.  buf ends in natural order.
+template <class E, bool DFT>
+__device__ double correlate_transform(E* buf, const PlanDev<E>& P, const E* __restrict__ v) {
+  using R = typename FT<E>::R;
+  const double s = load_zero_filled(buf, P, v, (R)rsqrt((double)P.N));
+  transform_adjoint<E, DFT>(buf, P);
+  return s;
+}
+
+// h = A^H zf(y - S_Omega A x_Lambda) for s atoms (lam[k], x[k]): a forward
+// transform of the zero-filled coefficients, the masked residual on Omega,
+// one adjoint transform.  buf ends in natural order.
+template <class E, bool DFT>
+__device__ void correlate_residual(E* buf, const PlanDev<E>& P, const E* __restrict__ y,
+                                   const int* lam, const E* xw, int s) {
+  using R = typename FT<E>::R;
+  const int N = P.N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) buf[swz<E>(i)] = zero<E>();
+  __syncthreads();
+  for (int k = threadIdx.x; k < s; k += blockDim.x) buf[swz<E>(lam[k])] = xw[k];
+  __syncthreads();
+  transform_forward<E, DFT>(buf, P);
+  // buf holds F x (unnormalised).  Write N^{-1/2} y - N^{-1} F x on Omega and
+  // zero elsewhere; the unnormalised adjoint then yields
+  // N^{-1/2} F^H zf(y) - N^{-1} F^H S^T S F x = A^H zf(y - S A x).
+  const R sy = (R)rsqrt((double)N), sx = (R)(1.0 / (double)N);
+  for (int pos = threadIdx.x; pos < N; pos += blockDim.x) {
+    const int m = __ldg(P.slot + pos);
+    const int a = swz<E>(pos);
+    buf[a] = m >= 0 ? sub(scale(y[m], sy), scale(buf[a], sx)) : zero<E>();
+  }
+  __syncthreads();
+  transform_adjoint<E, DFT>(buf, P);
+}
+
+// Load c into shared memory for the fast correlation.  With `doubled` (DFT
+// only) c is stored twice over so that c[(j - l) mod N + T e] is read at an
+// immediate offset without a wrap test; otherwise the index is masked.
+template <class E, bool DFT>
+__device__ void load_kernel_vector(E* cb, const PlanDev<E>& P, bool doubled) {
+  const int n = (DFT && doubled) ? 2 * P.N : P.N;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) cb[i] = __ldg(P.c + (i & (P.N - 1)));
+  __syncthreads();
+}
+
+// One chunk of CH outputs per thread: j = j0 + T e, e < CH.
+template <class E, bool DFT, bool DBL, int CH>
+__device__ __forceinline__ void fast_chunks(const E* cb, const E* h0, const int* lam,
+                                            const E* xw, int s, int N, const uint32_t* bits,
+                                            E* __restrict__ h_out, typename NormT<E>::V& bv, int& bj) {
+  using V = typename NormT<E>::V;
+  const int T = blockDim.x;
+  for (int j0 = threadIdx.x; j0 < N; j0 += T * CH) {
+    E acc[CH];
+#pragma unroll
+    for (int e = 0; e < CH; ++e) acc[e] = h0[j0 + T * e];
+    for (int k = 0; k < s; ++k) {
+      const int l = lam[k];
+      const E xv = xw[k];
+      if constexpr (DFT && DBL) {
+        const E* cp = cb + ((j0 - l) & (N - 1));
+#pragma unroll
+        for (int e = 0; e < CH; ++e) acc[e] = fnms(acc[e], xv, cp[T * e]);
+      } else if constexpr (DFT) {
+#pragma unroll
+        for (int e = 0; e < CH; ++e) acc[e] = fnms(acc[e], xv, cb[(j0 + T * e - l) & (N - 1)]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < CH; ++e) acc[e] = fnms(acc[e], xv, cb[(j0 + T * e) ^ l]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < CH; ++e) {
+      const int j = j0 + T * e;
+      if (h_out) h_out[j] = acc[e];
+      const V v = (bits && in_bits(bits, j)) ? (V)-1 : (V)norm2(acc[e]);
+      if (better(v, j, bv, bj)) { bv = v; bj = j; }
+    }
+  }
+}
+
+template <class E, bool DFT, bool DBL>
+__device__ __forceinline__ void fast_dispatch(const E* cb, const E* h0, const int* lam, const E* xw, int s, int N,
+                                              const uint32_t* bits, E* __restrict__ h_out,
+                                              typename NormT<E>::V& bv, int& bj) {
+  const int per = N / blockDim.x;  // outputs per thread (power of two, or 0 when N < T)
+  if (per >= 8) fast_chunks<E, DFT, DBL, 8>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  else if (per >= 4) fast_chunks<E, DFT, DBL, 4>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  else if (per >= 2) fast_chunks<E, DFT, DBL, 2>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  else fast_chunks<E, DFT, DBL, 1>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+}
+
+// h(j) = h0(j) - sum_{k<s} x_k c(j (-) lam_k) for all j (Eq. kernelsumOMP),
+// then the arg-max over j not in `bits`.  cb is c in shared memory, stored
+// twice over when `doubled` (DFT).
+template <class E, bool DFT>
+__device__ int correlate_fast(const E* cb, const E* h0, const int* lam, const E* xw,
+                              int s, int N, const uint32_t* bits, E* __restrict__ h_out,
+                              typename NormT<E>::V* rv, int* rj, bool doubled) {
+  using V = typename NormT<E>::V;
+  V bv = (V)-1;
+  int bj = 0x7fffffff;
+  if (DFT && doubled) fast_dispatch<E, DFT, true>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  else fast_dispatch<E, DFT, false>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  return block_argmax(bv, bj, rv, rj);
+}
+
+// Whether the fast correlation stores c twice over (DFT, when 2N elements
+// fit in 128 KB of shared memory).
+template <class E>
+__host__ __device__ inline bool kernel_doubled(int N) {
+  return FT<E>::C && 2 * (size_t)N * sizeof(E) <= (size_t)128 * 1024;
+}
+
+// ------------------------------------------------------------------------
+// FP64 least squares (Algorithm 1.1 step 6) by an explicit inverse Cholesky
+// factor.  With G_p = Phi_p^H Phi_p = L L^H, the library keeps B = L^{-1}
+// (packed lower triangle, row i at i(i+1)/2, in global memory), z = L^{-1} b
+// with b_k = h_0(lambda_k) = (Phi^H y)(lambda_k), and x = B^H z.  Adding
+// column lambda with Gram column g_k = c(lambda_k (-) lambda) (Eq. kernelsum):
+//   u = B g,  d^2 = c(0) - ||u||^2,  zeta = (b_p - u^H z) / d,
+//   row p of B = [-(u^H B) / d, 1 / d],   x += zeta * conj(row p of B),
+//   ||r||^2 -= |zeta|^2.
+// Both products with B are spread over every thread with rows (columns)
+// paired i <-> p-1-i so that all lanes carry equal work.
+template <class W>
+struct LsSmem {
+  W* z;     // [Kmax]
+  W* x;     // [Kmax]
+  W* g;     // [Kmax]  Gram column, then u
+  W* part;  // [2T]    partial sums
+};
+
+__device__ __forceinline__ int pidx(int i) { return (i * (i + 1)) >> 1; }
+
+// Layout of the paired, chunked triangular products: row (column) pairs
+// i <-> p-1-i over lanes, the concatenated pair split into `chunks` slices
+// over warps.  When there are more pairs than threads, each thread walks
+// pairs with stride T and chunks = 1.
+struct PairSplit {
+  int P2, chunks, pair, chunk, stride;
+  __device__ PairSplit(int p) {
+    P2 = (p + 1) >> 1;
+    const int T = blockDim.x;
+    int lanes = ((P2 + 31) >> 5) << 5;
+    if (lanes == 0) lanes = 32;
+    chunks = lanes <= T ? T / lanes : 1;
+    stride = lanes <= T ? lanes : T;
+    pair = threadIdx.x % stride;
+    chunk = threadIdx.x / stride;
+  }
+};
+
+// u_i = sum_{k<=i} B[i][k] g_k, i < p; result overwrites g.  part holds
+// max(2T, p) elements.  B is read with plain loads: it is written by the
+// same kernel.
+template <class W>
+__device__ void tri_matvec(const W* B, W* g, W* part, int p) {
+  if (p == 0) return;
+  PairSplit ps(p);
+  if (ps.chunk < ps.chunks) {
+    for (int pr = ps.pair; pr < ps.P2; pr += ps.stride) {
+      const int ra = pr, rb = p - 1 - pr;
+      const int la = ra + 1, lc = (rb != ra) ? la + rb + 1 : la;
+      const int q0 = (ps.chunk * lc) / ps.chunks, q1 = ((ps.chunk + 1) * lc) / ps.chunks;
+      W aa = W{}, ab = W{};
+      const W* Ba = B + pidx(ra);
+      const W* Bb = B + pidx(rb);
+      for (int q = q0; q < q1; ++q) {
+        if (q < la) aa = fmav(aa, Ba[q], g[q]);
+        else ab = fmav(ab, Bb[q - la], g[q - la]);
+      }
+      part[ps.chunk * p + ra] = aa;
+      if (rb != ra) part[ps.chunk * p + rb] = ab;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    W s = part[i];
+    for (int c = 1; c < ps.chunks; ++c) s = add(s, part[c * p + i]);
+    g[i] = s;
+  }
+  __syncthreads();
+}
+
+// w_k = scl * sum_{i=k}^{p-1} conj(u_i) B[i][k], k < p, written to row p of
+// B and to part[0..p).
+template <class W>
+__device__ void tri_vecmat_row(W* B, const W* u, W* part, int p, double scl) {
+  if (p == 0) return;
+  PairSplit ps(p);
+  if (ps.chunk < ps.chunks) {
+    for (int pr = ps.pair; pr < ps.P2; pr += ps.stride) {
+      const int ka = pr, kb = p - 1 - pr;
+      const int la = p - ka, lc = (kb != ka) ? la + (p - kb) : la;
+      const int q0 = (ps.chunk * lc) / ps.chunks, q1 = ((ps.chunk + 1) * lc) / ps.chunks;
+      W aa = W{}, ab = W{};
+      for (int q = q0; q < q1; ++q) {
+        if (q < la) { const int i = ka + q; aa = fmacv(aa, u[i], B[pidx(i) + ka]); }
+        else { const int i = kb + (q - la); ab = fmacv(ab, u[i], B[pidx(i) + kb]); }
+      }
+      part[ps.chunk * p + ka] = aa;
+      if (kb != ka) part[ps.chunk * p + kb] = ab;
+    }
+  }
+  __syncthreads();
+  // part[k] (chunk 0) is only ever read by the thread that owns column k
+  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+    W s = part[k];
+    for (int c = 1; c < ps.chunks; ++c) s = add(s, part[c * p + k]);
+    s = scale(s, scl);
+    part[k] = s;
+    B[pidx(p) + k] = s;
+  }
+  __syncthreads();
+}
+
+}  // namespace csf

@@ -1,0 +1,52 @@
+// Host-side interface between the C ABI (cs_api.cu) and the kernel
+// launchers (cs_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace csf {
+
+constexpr int kThreads = 256;
+constexpr int kMaxLogN = 13;   // N <= 8192: one instance per CTA
+constexpr int kMaxK = 1024;
+
+// Type-erased view of a plan's device tables.
+struct PlanView {
+  int N, logN, M;
+  bool dft, fp32;
+  const int* slot;
+  const void* tw64;   // double2 [N] (DFT)
+  const void* tw32;   // float2 [N]  (DFT, FP32)
+  const void* c64;    // double / double2 [N]
+  const void* c32;    // float / float2 [N] (FP32)
+};
+
+struct OmpLaunch {
+  const void* y;
+  int64_t batch;
+  int K;
+  double rel_tol;
+  int path, t_switch;
+  void* x_out;
+  int* supp_out;
+  int* iters_out;
+  double* res_out;
+};
+
+// plan construction
+cudaError_t launch_twiddles(const PlanView& P, void* tw64, void* tw32, cudaStream_t st);
+cudaError_t launch_kernel_vector(const PlanView& P, void* c64, void* c32, cudaStream_t st);
+
+// transforms / correlations
+cudaError_t launch_correlate(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax,
+                             cudaStream_t st);
+cudaError_t launch_correlate_fast(const PlanView& P, const void* h0, const int32_t* supp, const void* x,
+                                  int s, int64_t batch, void* h, int32_t* amax, cudaStream_t st);
+
+// OMP: workspace sizing then launch
+size_t omp_smem_bytes(const PlanView& P, int K, int path);
+int omp_grid(const PlanView& P, int K, int path, int64_t batch, int* err);
+size_t omp_workspace_bytes(const PlanView& P, int K, int grid);
+cudaError_t launch_omp(const PlanView& P, const OmpLaunch& a, void* ws, int grid, cudaStream_t st);
+
+}  // namespace csf

@@ -276,3 +276,12 @@ def test_dependent_column_stops():
     y = Phi[:, 0] + 0.5 * Phi[:, 1]
     res = omp.omp(Phi, y, 4, rel_tol=0.0)
     assert res["iters"] == 2 and res["halt"] == "dependent"
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_sensing_rows_match_dense(kind):
+    rng = np.random.default_rng(8)
+    N, M = 128, 50
+    om = synth.draw_omega(N, M, rng)
+    assert np.allclose(matrices.sensing_rows(kind, N, om), matrices.sensing(kind, N, om), atol=1e-13)
+    assert np.allclose(kernelsum.kernel_vector_rows(kind, N, om), kernelsum.kernel_vector(kind, N, om), atol=1e-13)
