@@ -59,8 +59,8 @@ __device__ int argmax_buffer(const E* buf, int N, const uint32_t* bits, E* __res
 }
 
 // buf <- scale * zf_Omega(v) in the position order the adjoint chain expects;
-// returns sum |v_m|^2 over this thread's entries (FP64).
-template <class E>
+// with NORM, returns sum |v_m|^2 over this thread's entries (FP64).
+template <class E, bool NORM>
 __device__ double load_zero_filled(E* buf, const PlanDev<E>& P, const E* __restrict__ v,
                                    typename FT<E>::R scl) {
   double s = 0.0;
@@ -69,7 +69,7 @@ __device__ double load_zero_filled(E* buf, const PlanDev<E>& P, const E* __restr
     E e = zero<E>();
     if (m >= 0) {
       const E vm = v[m];
-      s += norm2(to_w(vm));
+      if constexpr (NORM) s += norm2(to_w(vm));
       e = scale(vm, scl);
     }
     buf[swz<E>(pos)] = e;
@@ -78,11 +78,18 @@ __device__ double load_zero_filled(E* buf, const PlanDev<E>& P, const E* __restr
   return s;
 }
 
+// 1/sqrt(N) for N = 2^logN, exact to the working precision without FP64 math
+template <class R>
+__device__ __forceinline__ R inv_sqrt_pow2(int logN) {
+  const R r = (R)1 / (R)(1 << (logN >> 1));
+  return (logN & 1) ? r * (R)0.70710678118654752440 : r;
+}
+
 // h = A^H zf_Omega(v): one adjoint transform.  buf ends in natural order.
-template <class E, bool DFT>
+template <class E, bool DFT, bool NORM = false>
 __device__ double correlate_transform(E* buf, const PlanDev<E>& P, const E* __restrict__ v) {
   using R = typename FT<E>::R;
-  const double s = load_zero_filled(buf, P, v, (R)rsqrt((double)P.N));
+  const double s = load_zero_filled<E, NORM>(buf, P, v, inv_sqrt_pow2<R>(P.logN));
   transform_adjoint<E, DFT>(buf, P);
   return s;
 }
@@ -103,7 +110,7 @@ __device__ void correlate_residual(E* buf, const PlanDev<E>& P, const E* __restr
   // buf holds F x (unnormalised).  Write N^{-1/2} y - N^{-1} F x on Omega and
   // zero elsewhere; the unnormalised adjoint then yields
   // N^{-1/2} F^H zf(y) - N^{-1} F^H S^T S F x = A^H zf(y - S A x).
-  const R sy = (R)rsqrt((double)N), sx = (R)(1.0 / (double)N);
+  const R sy = inv_sqrt_pow2<R>(P.logN), sx = (R)1 / (R)N;
   for (int pos = threadIdx.x; pos < N; pos += blockDim.x) {
     const int m = __ldg(P.slot + pos);
     const int a = swz<E>(pos);
@@ -215,8 +222,9 @@ __device__ __forceinline__ int pidx(int i) { return (i * (i + 1)) >> 1; }
 
 // Layout of the paired, chunked triangular products: row (column) pairs
 // i <-> p-1-i over lanes, the concatenated pair split into `chunks` slices
-// over warps.  When there are more pairs than threads, each thread walks
-// pairs with stride T and chunks = 1.
+// over warps, at most T / (2 lanes) of them so that the partial sums fit in
+// max(T, p) elements (4 warps, one per SM sub-partition, when p <= 64).  When
+// there are more pairs than threads, each thread walks pairs with stride T.
 struct PairSplit {
   int P2, chunks, pair, chunk, stride;
   __device__ PairSplit(int p) {
@@ -224,7 +232,8 @@ struct PairSplit {
     const int T = blockDim.x;
     int lanes = ((P2 + 31) >> 5) << 5;
     if (lanes == 0) lanes = 32;
-    chunks = lanes <= T ? T / lanes : 1;
+    chunks = T / (2 * lanes);
+    if (chunks < 1) chunks = 1;
     stride = lanes <= T ? lanes : T;
     pair = threadIdx.x % stride;
     chunk = threadIdx.x / stride;
@@ -232,7 +241,7 @@ struct PairSplit {
 };
 
 // u_i = sum_{k<=i} B[i][k] g_k, i < p; result overwrites g.  part holds
-// max(2T, p) elements.  B is read with plain loads: it is written by the
+// max(T, p) elements.  B is read with plain loads: it is written by the
 // same kernel.
 template <class W>
 __device__ void tri_matvec(const W* B, W* g, W* part, int p) {
@@ -243,15 +252,22 @@ __device__ void tri_matvec(const W* B, W* g, W* part, int p) {
       const int ra = pr, rb = p - 1 - pr;
       const int la = ra + 1, lc = (rb != ra) ? la + rb + 1 : la;
       const int q0 = (ps.chunk * lc) / ps.chunks, q1 = ((ps.chunk + 1) * lc) / ps.chunks;
-      W aa = W{}, ab = W{};
+      // One accumulator and one FMA per position, whichever row the position
+      // falls in: the row switch is a register move, not a second FMA path.
+      W acc = W{}, first = W{};
+      const W* Bb = B + pidx(rb) - la;
+      const W* gb = g - la;
       const W* Ba = B + pidx(ra);
-      const W* Bb = B + pidx(rb);
       for (int q = q0; q < q1; ++q) {
-        if (q < la) aa = fmav(aa, Ba[q], g[q]);
-        else ab = fmav(ab, Bb[q - la], g[q - la]);
+        const bool second = q >= la;
+        if (q == la) { first = acc; acc = W{}; }
+        acc = fmav(acc, second ? Bb[q] : Ba[q], second ? gb[q] : g[q]);
       }
-      part[ps.chunk * p + ra] = aa;
-      if (rb != ra) part[ps.chunk * p + rb] = ab;
+      const bool ended_in_b = q1 > la;
+      const W pa = ended_in_b ? (q0 < la ? first : W{}) : acc;
+      const W pb = ended_in_b ? acc : W{};
+      part[ps.chunk * p + ra] = pa;
+      if (rb != ra) part[ps.chunk * p + rb] = pb;
     }
   }
   __syncthreads();
@@ -274,13 +290,18 @@ __device__ void tri_vecmat_row(W* B, const W* u, W* part, int p, double scl) {
       const int ka = pr, kb = p - 1 - pr;
       const int la = p - ka, lc = (kb != ka) ? la + (p - kb) : la;
       const int q0 = (ps.chunk * lc) / ps.chunks, q1 = ((ps.chunk + 1) * lc) / ps.chunks;
-      W aa = W{}, ab = W{};
+      W acc = W{}, first = W{};
       for (int q = q0; q < q1; ++q) {
-        if (q < la) { const int i = ka + q; aa = fmacv(aa, u[i], B[pidx(i) + ka]); }
-        else { const int i = kb + (q - la); ab = fmacv(ab, u[i], B[pidx(i) + kb]); }
+        const bool second = q >= la;
+        if (q == la) { first = acc; acc = W{}; }
+        const int i = second ? kb + (q - la) : ka + q;
+        acc = fmacv(acc, u[i], B[pidx(i) + (second ? kb : ka)]);
       }
-      part[ps.chunk * p + ka] = aa;
-      if (kb != ka) part[ps.chunk * p + kb] = ab;
+      const bool ended_in_b = q1 > la;
+      const W pa = ended_in_b ? (q0 < la ? first : W{}) : acc;
+      const W pb = ended_in_b ? acc : W{};
+      part[ps.chunk * p + ka] = pa;
+      if (kb != ka) part[ps.chunk * p + kb] = pb;
     }
   }
   __syncthreads();

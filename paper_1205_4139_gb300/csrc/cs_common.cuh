@@ -124,7 +124,9 @@ template <class E> __device__ __forceinline__ int swz(int i) {
 // ------------------------------------------------- in-register butterflies
 __host__ __device__ constexpr int ilog2c(int r) { return r <= 1 ? 0 : 1 + ilog2c(r >> 1); }
 __host__ __device__ constexpr int bitrevc(int q, int bits) {
-  return bits == 0 ? 0 : (((q & 1) << (bits - 1)) | bitrevc(q >> 1, bits - 1));
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((q >> i) & 1) << (bits - 1 - i);
+  return r;
 }
 
 // cos(pi k / 8) for any integer k, and sin(pi k / 8) = cos(pi (k - 4) / 8)
@@ -174,37 +176,42 @@ __device__ __forceinline__ E rot_pi8(E t, int k) {
 
 // In-place radix-2 decimation-in-frequency DFT of R values held in
 // registers: V_q = sum_r v_r exp(SIGN 2 pi i r q / R).  On return v[k] holds
-// V_{bitrev(k)}.
-template <int R, int SIGN, class E>
-__device__ __forceinline__ void dft_reg(E (&v)[R]) {
+// V_{bitrev(k)}.  Stages recurse on the half-span H at compile time so that
+// every register index is a constant.
+template <int R, int SIGN, int H, class E>
+__device__ __forceinline__ void dft_stage(E (&v)[R]) {
 #pragma unroll
-  for (int h = R / 2; h >= 1; h >>= 1) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      if ((i & h) == 0) {
-        E a = v[i], b = v[i + h];
-        v[i] = add(a, b);
-        const int e = (i & (h - 1)) * (R / (2 * h));  // power of exp(SIGN 2 pi i / R)
-        v[i + h] = rot_pi8<SIGN>(sub(a, b), (16 / R) * e);
-      }
+  for (int i = 0; i < R; ++i) {
+    if ((i & H) == 0) {
+      E a = v[i], b = v[i + H];
+      v[i] = add(a, b);
+      const int e = (i & (H - 1)) * (R / (2 * H));  // power of exp(SIGN 2 pi i / R)
+      v[i + H] = rot_pi8<SIGN>(sub(a, b), (16 / R) * e);
     }
   }
+  if constexpr (H > 1) dft_stage<R, SIGN, H / 2>(v);
+}
+template <int R, int SIGN, class E>
+__device__ __forceinline__ void dft_reg(E (&v)[R]) {
+  if constexpr (R > 1) dft_stage<R, SIGN, R / 2>(v);
 }
 
 // In-place Sylvester Hadamard butterflies (natural order in and out).
-template <int R, class E>
-__device__ __forceinline__ void wht_reg(E (&v)[R]) {
+template <int R, int H, class E>
+__device__ __forceinline__ void wht_stage(E (&v)[R]) {
 #pragma unroll
-  for (int h = R / 2; h >= 1; h >>= 1) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      if ((i & h) == 0) {
-        E a = v[i], b = v[i + h];
-        v[i] = add(a, b);
-        v[i + h] = sub(a, b);
-      }
+  for (int i = 0; i < R; ++i) {
+    if ((i & H) == 0) {
+      E a = v[i], b = v[i + H];
+      v[i] = add(a, b);
+      v[i + H] = sub(a, b);
     }
   }
+  if constexpr (H > 1) wht_stage<R, H / 2>(v);
+}
+template <int R, class E>
+__device__ __forceinline__ void wht_reg(E (&v)[R]) {
+  if constexpr (R > 1) wht_stage<R, R / 2>(v);
 }
 
 // --------------------------------------------------------------- reductions

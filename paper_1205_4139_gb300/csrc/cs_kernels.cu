@@ -28,16 +28,16 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 // DIF twiddles W_{L_p}^{n q} = exp(-2 pi i n q / L_p) of every pass, FP64
 // via sincospi (exact argument: L_p is a power of two) and rounded to FP32.
 __global__ void twiddle_kernel(int logN, double2* tw64, float2* tw32) {
-  const Sched s = make_sched(logN);
-  for (int p = 0; p < s.P; ++p) {
-    const int R = 1 << s.logR[p], L = s.L[p], S = L / R;
+  const int N = 1 << logN, P = sched_passes(logN);
+  for (int p = 0; p < P; ++p) {
+    const int L = 1 << sched_logL(logN, p), R = 1 << sched_logR(logN, p), S = L / R, off = N - L;
     const int cnt = (R - 1) * S;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
       const int q = i / S + 1, n = i % S;
       double sn, cs;
       sincospi(-2.0 * (double)(n * q) / (double)L, &sn, &cs);
-      tw64[s.off[p] + i] = make_double2(cs, sn);
-      if (tw32) tw32[s.off[p] + i] = make_float2((float)cs, (float)sn);
+      tw64[off + i] = make_double2(cs, sn);
+      if (tw32) tw32[off + i] = make_float2((float)cs, (float)sn);
     }
   }
 }
@@ -228,7 +228,7 @@ __host__ __device__ inline OmpSmem<E> omp_layout(int N, int K, int path, int T) 
   L.z = o;    o = a16(o + (size_t)Kc * sizeof(W));
   L.x = o;    o = a16(o + (size_t)Kc * sizeof(W));
   L.g = o;    o = a16(o + (size_t)Kc * sizeof(W));
-  L.part = o; o = a16(o + (size_t)(2 * T > Kc ? 2 * T : Kc) * sizeof(W));
+  L.part = o; o = a16(o + (size_t)(T > Kc ? T : Kc) * sizeof(W));
   L.xw = o;   o = a16(o + (size_t)Kc * sizeof(E));
   L.red = o;  o = a16(o + (size_t)(32 * 4 + 4) * sizeof(double));
   L.rv = o;   o = a16(o + 34 * sizeof(V));
@@ -240,7 +240,7 @@ __host__ __device__ inline OmpSmem<E> omp_layout(int N, int K, int path, int T) 
 }
 
 template <class E>
-__global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs<E> a) {
+__global__ void __launch_bounds__(kThreads, (sizeof(E) > 8 ? 2 : 3)) omp_kernel(OmpArgs<E> a) {
   using W = typename FT<E>::W;
   using V = typename NormT<E>::V;
   constexpr bool DFT = FT<E>::C;
@@ -258,7 +258,9 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs<E> a) {
   int* rj = (int*)(sm + Ls.rj);
   int* lam = (int*)(sm + Ls.lam);
   uint32_t* bits = (uint32_t*)(sm + Ls.bits);
-  __shared__ int s_inst;
+  __shared__ int s_inst, s_state;
+  __shared__ double s_rn2, s_invd;
+  __shared__ W s_zeta;
   const int nbits = (N + 31) >> 5;
   const bool dbl = kernel_doubled<E>(N);
 
@@ -278,11 +280,11 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs<E> a) {
     for (int i = tid; i < nbits; i += T) bits[i] = 0u;
 
     // t = 1: h_0 = Phi^H y by one transform (Eq. kernelsumOMP, first case)
-    double yy[1] = {correlate_transform<E, DFT>(regA, a.P, y)};
+    double yy[1] = {correlate_transform<E, DFT, true>(regA, a.P, y)};
     block_sum(yy, red);
     const double ynorm2 = yy[0];
     int p = 0;
-    double rn2 = ynorm2;
+    if (tid == 0) s_rn2 = ynorm2;
     if (ynorm2 > 0.0 && K > 0) {
       int lnew = argmax_buffer(regA, N, nullptr, h0, rv, rj);  // step 3, and h_0 kept for later
       bool c_in_smem = false;
@@ -294,36 +296,62 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs<E> a) {
         }
         __syncthreads();
         tri_matvec(B, g, part, p);                           // g <- u = B g
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int k = tid; k < p; k += T) {
-          acc[0] += norm2(g[k]);
-          const W t = cmul(g[k], z[k]);
-          acc[1] += re(t);
-          acc[2] += im(t);
+        // Scalar FP64 work by one warp only: on this part every FP64 warp
+        // instruction costs the same whatever its active lanes, so the other
+        // warps wait at the barrier instead of repeating it.
+        if (tid < 32) {
+          double an = 0.0, ar = 0.0, ai = 0.0;
+          for (int k = tid; k < p; k += 32) {
+            an += norm2(g[k]);
+            const W t = cmul(g[k], z[k]);
+            ar += re(t);
+            ai += im(t);
+          }
+          an = warp_sum(an);
+          ar = warp_sum(ar);
+          if constexpr (DFT) ai = warp_sum(ai);
+          if (tid == 0) {
+            const double d2 = c0 - an;
+            int st = 0;
+            if (!(d2 > dep)) {
+              st = 1;                                        // column dependent on Lambda
+            } else {
+              const double invd = 1.0 / sqrt(d2);
+              const W bp = to_w(h0[lnew]);                    // (Phi^H y)(lambda_new)
+              const W zeta = scale(sub(bp, make_w<W>(ar, ai)), invd);
+              const double r2 = s_rn2 - norm2(zeta);
+              s_rn2 = r2;
+              s_invd = invd;
+              s_zeta = zeta;
+              if (p + 1 >= K || r2 < tol2 * ynorm2) st = 2;  // step 8 after this column
+            }
+            s_state = st;
+          }
         }
-        block_sum(acc, red);
-        const double d2 = c0 - acc[0];
-        if (!(d2 > dep)) break;                              // column dependent on Lambda
-        const double invd = 1.0 / sqrt(d2);
-        const W bp = to_w(h0[lnew]);                          // (Phi^H y)(lambda_new)
-        const W zeta = scale(sub(bp, make_w<W>(acc[1], acc[2])), invd);
+        __syncthreads();
+        const int st = s_state;
+        if (st == 1) break;
+        const double invd = s_invd;
+        const W zeta = s_zeta;
         tri_vecmat_row(B, g, part, p, -invd);                // row p of B (part[0..p))
-        for (int k = tid; k < p; k += T) x[k] = fmacv(x[k], part[k], zeta);
+        for (int k = tid; k < p; k += T) {
+          const W xk = fmacv(x[k], part[k], zeta);
+          x[k] = xk;
+          xw[k] = from_w<E>(xk);
+        }
         if (tid == 0) {
           B[pidx(p) + p] = make_w<W>(invd, 0.0);
           z[p] = zeta;
-          x[p] = scale(zeta, invd);
+          const W xp = scale(zeta, invd);
+          x[p] = xp;
+          xw[p] = from_w<E>(xp);
           lam[p] = lnew;
           bits[lnew >> 5] |= 1u << (lnew & 31);
         }
         __syncthreads();
-        rn2 -= norm2(zeta);
         ++p;
-        for (int k = tid; k < p; k += T) xw[k] = from_w<E>(x[k]);
-        __syncthreads();
         // ---- step 8: halting ----
-        if (p >= K) break;
-        if (rn2 < tol2 * ynorm2) break;
+        if (st == 2) break;
         // ---- steps 2-3 at t = p + 1 ----
         const int t = p + 1;
         const bool fast = a.path == PATH_FAST || (a.path == PATH_HYBRID && t <= a.t_switch);
@@ -344,7 +372,7 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs<E> a) {
     }
     if (tid == 0) {
       if (a.iters_out) a.iters_out[b] = p;
-      if (a.res_out) a.res_out[b] = ynorm2 > 0.0 ? sqrt(fmax(rn2, 0.0) / ynorm2) : 0.0;
+      if (a.res_out) a.res_out[b] = ynorm2 > 0.0 ? sqrt(fmax(s_rn2, 0.0) / ynorm2) : 0.0;
     }
     __syncthreads();
   }

@@ -25,40 +25,24 @@
 
 namespace csf {
 
-struct Sched {
-  int P;          // number of passes
-  int logR[8];    // log2 radix of each DIF pass
-  int L[8];       // sub-transform length of each DIF pass
-  int off[8];     // twiddle-table offset of each DIF pass
-};
-
-__host__ __device__ inline Sched make_sched(int logN) {
-  Sched s;
-  s.P = 0;
-  int rem = logN;
-  while (rem >= 4) { s.logR[s.P++] = 4; rem -= 4; }
-  if (rem > 0) s.logR[s.P++] = rem;
-  int L = 1 << logN, off = 0;
-  for (int p = 0; p < s.P; ++p) {
-    const int R = 1 << s.logR[p];
-    s.L[p] = L;
-    s.off[p] = off;
-    off += (R - 1) * (L / R);
-    L /= R;
-  }
-  return s;
+// Pass p of the DIF chain: L_p = N >> 4p, radix 2^min(4, log2 L_p), and the
+// twiddle-table offset sum_{q<p} (R_q - 1) L_q / R_q = N - L_p.
+__host__ __device__ inline int sched_passes(int logN) { return (logN + 3) >> 2; }
+__host__ __device__ inline int sched_logL(int logN, int p) { return logN - 4 * p; }
+__host__ __device__ inline int sched_logR(int logN, int p) {
+  const int l = logN - 4 * p;
+  return l < 4 ? l : 4;
 }
 
 // Position of frequency k after the forward DIF chain (host and device).
 __host__ __device__ inline int dif_position(int k, int logN) {
-  Sched s = make_sched(logN);
-  int pos = 0, L = 1 << logN;
-  for (int p = 0; p < s.P; ++p) {
-    const int R = 1 << s.logR[p];
-    const int q = k & (R - 1);
-    k >>= s.logR[p];
-    L /= R;            // stride of digit q in the stored position
-    pos += q * L;
+  int pos = 0;
+  const int P = sched_passes(logN);
+  for (int p = 0; p < P; ++p) {
+    const int lr = sched_logR(logN, p);
+    const int q = k & ((1 << lr) - 1);
+    k >>= lr;
+    pos += q << (sched_logL(logN, p) - lr);  // digit q has stride S_p = L_p / R_p
   }
   return pos;
 }
@@ -130,15 +114,15 @@ __device__ __forceinline__ void wht_pass(E* buf, int N, int S) {
 // digit-reversed order out.  buf must be visible to all threads on entry.
 template <class E>
 __device__ void dft_forward(E* buf, int logN, const E* __restrict__ tw) {
-  const Sched s = make_sched(logN);
-  const int N = 1 << logN;
-  for (int p = 0; p < s.P; ++p) {
-    const E* t = tw + s.off[p];
-    switch (s.logR[p]) {
-      case 4: dif_pass<16>(buf, N, s.L[p], t); break;
-      case 3: dif_pass<8>(buf, N, s.L[p], t); break;
-      case 2: dif_pass<4>(buf, N, s.L[p], t); break;
-      default: dif_pass<2>(buf, N, s.L[p], t); break;
+  const int N = 1 << logN, P = sched_passes(logN);
+  for (int p = 0; p < P; ++p) {
+    const int L = 1 << sched_logL(logN, p);
+    const E* t = tw + (N - L);
+    switch (sched_logR(logN, p)) {
+      case 4: dif_pass<16>(buf, N, L, t); break;
+      case 3: dif_pass<8>(buf, N, L, t); break;
+      case 2: dif_pass<4>(buf, N, L, t); break;
+      default: dif_pass<2>(buf, N, L, t); break;
     }
   }
 }
@@ -147,15 +131,15 @@ __device__ void dft_forward(E* buf, int logN, const E* __restrict__ tw) {
 // natural order out.
 template <class E>
 __device__ void dft_adjoint(E* buf, int logN, const E* __restrict__ tw) {
-  const Sched s = make_sched(logN);
-  const int N = 1 << logN;
-  for (int p = s.P - 1; p >= 0; --p) {
-    const E* t = tw + s.off[p];
-    switch (s.logR[p]) {
-      case 4: dit_pass<16>(buf, N, s.L[p], t); break;
-      case 3: dit_pass<8>(buf, N, s.L[p], t); break;
-      case 2: dit_pass<4>(buf, N, s.L[p], t); break;
-      default: dit_pass<2>(buf, N, s.L[p], t); break;
+  const int N = 1 << logN, P = sched_passes(logN);
+  for (int p = P - 1; p >= 0; --p) {
+    const int L = 1 << sched_logL(logN, p);
+    const E* t = tw + (N - L);
+    switch (sched_logR(logN, p)) {
+      case 4: dit_pass<16>(buf, N, L, t); break;
+      case 3: dit_pass<8>(buf, N, L, t); break;
+      case 2: dit_pass<4>(buf, N, L, t); break;
+      default: dit_pass<2>(buf, N, L, t); break;
     }
   }
 }
