@@ -133,6 +133,28 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
                  void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev,
                  void* stream);
 
+/* cs_omp without any allocation by the library: the paper has no
+ * counterpart; this exists for callers that must not allocate device memory
+ * while they solve (cudaMalloc/cudaFree synchronise the device and may block,
+ * which a latency-bound request loop cannot take, and some processes give
+ * the library no device memory beyond their own buffers).  Same arguments,
+ * outputs and results as cs_omp.  Instead of the plan's growable workspace it
+ * uses one fixed 32 MiB device array that the library holds on every device
+ * that loads it until the process exits.
+ *   - The first call on a device looks up that array's device address with
+ *     cudaGetSymbolAddress (with the device current) and caches it; make that
+ *     first call before any stream capture.
+ *   - If one CTA's share (N working elements + K(K+1)/2 FP64 elements + 16
+ *     bytes) exceeds 32 MiB the call returns CS_ERR_UNSUPPORTED with a message
+ *     in cs_last_error; otherwise it runs as many resident CTAs as fit.
+ *   - Every call on a device shares the array and leaves its contents behind;
+ *     the call clears what must start at zero.  Calls that overlap on the GPU
+ *     (other streams, other threads, other plans) race on it: serialise them.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine. */
+cs_status cs_omp_noalloc(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K,
+                         const cs_halt* halt, void* x_dev, int32_t* supp_dev, int32_t* iters_dev,
+                         double* resnorm_dev, void* stream);
+
 /* Short static description of a status code. */
 const char* cs_status_string(cs_status s);
 

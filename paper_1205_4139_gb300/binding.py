@@ -23,7 +23,7 @@ PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 
 # Every function include/csfast.h declares.
 EXPORTS = ["cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_kernel", "cs_correlate",
-           "cs_correlate_fast", "cs_omp", "cs_status_string", "cs_last_error"]
+           "cs_correlate_fast", "cs_omp", "cs_omp_noalloc", "cs_status_string", "cs_last_error"]
 
 
 class CsError(RuntimeError):
@@ -55,8 +55,9 @@ def load(path: str = LIB_PATH):
     L.cs_correlate.argtypes = [vp, vp, i64, vp, vp, vp]
     L.cs_correlate_fast.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, vp]
     L.cs_omp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
+    L.cs_omp_noalloc.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     for f in ("cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_kernel", "cs_correlate",
-              "cs_correlate_fast", "cs_omp"):
+              "cs_correlate_fast", "cs_omp", "cs_omp_noalloc"):
         getattr(L, f).restype = ctypes.c_int
     L.cs_status_string.argtypes = [ctypes.c_int]
     L.cs_status_string.restype = ctypes.c_char_p

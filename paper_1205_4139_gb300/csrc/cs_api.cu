@@ -54,6 +54,13 @@ extern "C" const char* cs_status_string(cs_status s) {
 
 extern "C" const char* cs_last_error(void) { return g_err; }
 
+namespace csf {
+// accessors for the other translation units of the library
+const PlanView* plan_view(cs_plan_t plan) { return &plan->v; }
+int plan_t_switch_default(cs_plan_t plan) { return plan->t_switch_default; }
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace csf
+
 static void plan_free(cs_plan_s* p) {
   if (!p) return;
   cudaFree(p->d_slot);
