@@ -95,6 +95,12 @@ cs_status cs_plan_destroy(cs_plan_t plan);
 cs_status cs_plan_info(cs_plan_t plan, int64_t* N, int64_t* M, int32_t* kind, int32_t* prec,
                        int32_t* t_switch_default);
 
+/* Errors the kernels detected on the device since the last call (0 = none;
+ * bit 0: an OMP launch stopped because its phase loop reached its bound,
+ * which leaves that launch's outputs incomplete).  Synchronises `stream`,
+ * then clears the word. */
+cs_status cs_plan_status(cs_plan_t plan, int32_t* device_error, void* stream);
+
 /* Copy the correlation kernel vector c (Eq. kernelsum) into c_dev:
  * `prec` CS_FP64 gives double / double2 [N], CS_FP32 float / float2 [N]. */
 cs_status cs_plan_kernel(cs_plan_t plan, void* c_dev, int32_t prec, void* stream);

@@ -22,7 +22,7 @@ KINDS = {"wht": CS_WHT, "dft": CS_DFT}
 PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 
 # Every function include/csfast.h declares.
-EXPORTS = ["cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_kernel", "cs_correlate",
+EXPORTS = ["cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
            "cs_correlate_fast", "cs_omp", "cs_omp_noalloc", "cs_status_string", "cs_last_error"]
 
 
@@ -52,11 +52,12 @@ def load(path: str = LIB_PATH):
     L.cs_plan_destroy.argtypes = [vp]
     L.cs_plan_info.argtypes = [vp, pi64, pi64, pi32, pi32, pi32]
     L.cs_plan_kernel.argtypes = [vp, vp, i32, vp]
+    L.cs_plan_status.argtypes = [vp, pi32, vp]
     L.cs_correlate.argtypes = [vp, vp, i64, vp, vp, vp]
     L.cs_correlate_fast.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, vp]
     L.cs_omp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_omp_noalloc.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
-    for f in ("cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_kernel", "cs_correlate",
+    for f in ("cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
               "cs_correlate_fast", "cs_omp", "cs_omp_noalloc"):
         getattr(L, f).restype = ctypes.c_int
     L.cs_status_string.argtypes = [ctypes.c_int]
@@ -125,6 +126,12 @@ class Plan:
         _check(load().cs_plan_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(k), ctypes.byref(p),
                                    ctypes.byref(ts)))
         return {"N": n.value, "M": m.value, "kind": k.value, "prec": p.value, "t_switch_default": ts.value}
+
+    def device_error(self, stream=None) -> int:
+        """Kernel-detected error bits since the last call (cs_plan_status)."""
+        e = ctypes.c_int32()
+        _check(load().cs_plan_status(self._h, ctypes.byref(e), _stream(stream)))
+        return e.value
 
     def kernel_vector(self, prec: str = "fp64", stream=None):
         import torch

@@ -22,6 +22,7 @@ struct cs_plan_s {
   void* d_tw32 = nullptr;
   void* d_c64 = nullptr;
   void* d_c32 = nullptr;
+  int* d_status = nullptr;  // kernel-detected errors (cs_plan_status)
   void* ws = nullptr;       // OMP workspace (grows on demand, stream-ordered)
   size_t ws_bytes = 0;
 };
@@ -68,6 +69,7 @@ static void plan_free(cs_plan_s* p) {
   cudaFree(p->d_tw32);
   cudaFree(p->d_c64);
   cudaFree(p->d_c32);
+  cudaFree(p->d_status);
   cudaFree(p->ws);
   delete p;
 }
@@ -130,11 +132,14 @@ extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_
   }
   PLAN_TRY(cudaMalloc(&p->d_c64, (size_t)N * wb), "cudaMalloc c");
   if (prec == CS_FP32) PLAN_TRY(cudaMalloc(&p->d_c32, (size_t)N * wb / 2), "cudaMalloc c");
+  PLAN_TRY(cudaMalloc(&p->d_status, sizeof(int)), "cudaMalloc status");
+  PLAN_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st), "clear status");
   p->v.slot = p->d_slot;
   p->v.tw64 = p->d_tw64;
   p->v.tw32 = p->d_tw32;
   p->v.c64 = p->d_c64;
   p->v.c32 = p->d_c32;
+  p->v.status = p->d_status;
   if (kind == CS_DFT) PLAN_TRY(launch_twiddles(p->v, p->d_tw64, p->d_tw32, st), "twiddle kernel");
   PLAN_TRY(launch_kernel_vector(p->v, p->d_c64, p->d_c32, st), "kernel-vector kernel");
   PLAN_TRY(cudaStreamSynchronize(st), "plan synchronize");
@@ -158,6 +163,17 @@ extern "C" cs_status cs_plan_info(cs_plan_t plan, int64_t* N, int64_t* M, int32_
   if (kind) *kind = plan->kind;
   if (prec) *prec = plan->prec;
   if (t_switch_default) *t_switch_default = plan->t_switch_default;
+  return CS_OK;
+}
+
+extern "C" cs_status cs_plan_status(cs_plan_t plan, int32_t* device_error, void* stream) {
+  if (!plan || !device_error) return CS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  int h = 0;
+  CS_CUDA(cudaMemcpyAsync(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
+  CS_CUDA(cudaStreamSynchronize(st), "status synchronize");
+  CS_CUDA(cudaMemsetAsync(plan->d_status, 0, sizeof(int), st), "clear status");
+  *device_error = h;
   return CS_OK;
 }
 

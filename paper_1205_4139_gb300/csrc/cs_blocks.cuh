@@ -1,14 +1,15 @@
-// Block-level building blocks of the hot path, each run by one CTA on one
-// instance:
+// Building blocks of the hot path, each run by one group of warps (`Grp`) on
+// one instance:
 //   * correlate_transform  h = A^H zf_Omega(v)         (Algorithm 1.1 step 2)
 //   * correlate_residual   h = A^H zf(y - S A x_Lambda) (steps 7 and 2)
 //   * correlate_fast       h = h_0 - sum_k x_k c(j (-) lambda_k)
 //                                                      (Eq. kernelsumOMP)
 //   * each followed by the identification of step 3 (arg-max of |h|^2 over j
 //     not in Lambda, lowest j on ties)
-//   * ls_append            the FP64 least-squares update of step 6 for one
-//     new column, with the Gram column read off c (Eq. kernelsum).
+//   * tri_matvec / tri_vecmat_row, the two FP64 triangular products of the
+//     least-squares update of step 6 (Gram column read off c, Eq. kernelsum).
 #pragma once
+#include "cs_internal.h"
 #include "cs_transform.cuh"
 
 namespace csf {
@@ -23,48 +24,53 @@ struct PlanDev {
   const typename FT<E>::W* __restrict__ c64;  // correlation kernel vector, FP64 [N]
 };
 
+template <class E>
+inline PlanDev<E> plan_dev(const PlanView& P) {
+  PlanDev<E> d;
+  d.N = P.N;
+  d.logN = P.logN;
+  d.M = P.M;
+  d.slot = P.slot;
+  constexpr bool f32 = sizeof(typename FT<E>::R) == 4;
+  d.tw = (const E*)(f32 ? P.tw32 : P.tw64);
+  d.c = (const E*)(f32 ? P.c32 : P.c64);
+  d.c64 = (const typename FT<E>::W*)P.c64;
+  return d;
+}
+
 // |h|^2 type used for identification: the working precision.
 template <class E> struct NormT { using V = typename FT<E>::R; };
 
 // Unnormalised transform of the kind: DFT uses F^H (adjoint chain) for the
 // correlation and F (forward chain) for the synthesis; WHT uses H for both.
 template <class E, bool DFT>
-__device__ __forceinline__ void transform_adjoint(E* buf, const PlanDev<E>& P) {
-  if constexpr (DFT) dft_adjoint(buf, P.logN, P.tw);
-  else wht(buf, P.logN);
+__device__ __forceinline__ void transform_adjoint(const Grp& g, E* buf, const PlanDev<E>& P) {
+  if constexpr (DFT) dft_adjoint(g, buf, P.logN, P.tw);
+  else wht(g, buf, P.logN);
 }
 template <class E, bool DFT>
-__device__ __forceinline__ void transform_forward(E* buf, const PlanDev<E>& P) {
-  if constexpr (DFT) dft_forward(buf, P.logN, P.tw);
-  else wht(buf, P.logN);
+__device__ __forceinline__ void transform_forward(const Grp& g, E* buf, const PlanDev<E>& P) {
+  if constexpr (DFT) dft_forward(g, buf, P.logN, P.tw);
+  else wht(g, buf, P.logN);
 }
 
 __device__ __forceinline__ bool in_bits(const uint32_t* bits, int j) { return (bits[j >> 5] >> (j & 31)) & 1u; }
 
-// Arg-max of |buf(j)|^2 over j not flagged in `bits` (NULL: no exclusions);
-// optionally writes buf to h_out in natural order.
-template <class E>
-__device__ int argmax_buffer(const E* buf, int N, const uint32_t* bits, E* __restrict__ h_out,
-                             typename NormT<E>::V* rv, int* rj) {
-  using V = typename NormT<E>::V;
-  V bv = (V)-1;
-  int bj = 0x7fffffff;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const E h = buf[swz<E>(j)];
-    if (h_out) h_out[j] = h;
-    const V v = (bits && in_bits(bits, j)) ? (V)-1 : (V)norm2(h);
-    if (better(v, j, bv, bj)) { bv = v; bj = j; }
-  }
-  return block_argmax(bv, bj, rv, rj);
+// 1/sqrt(N) for N = 2^logN, exact to the working precision without FP64 math
+template <class R>
+__device__ __forceinline__ R inv_sqrt_pow2(int logN) {
+  const R r = (R)1 / (R)(1 << (logN >> 1));
+  return (logN & 1) ? r * (R)0.70710678118654752440 : r;
 }
 
-// buf <- scale * zf_Omega(v) in the position order the adjoint chain expects;
-// with NORM, returns sum |v_m|^2 over this thread's entries (FP64).
+// buf <- scl * zf_Omega(v) in the position order the adjoint chain expects
+// (unit stride over positions, so the slot-map reads coalesce); with NORM,
+// returns sum |v_m|^2 over this thread's entries (FP64).
 template <class E, bool NORM>
-__device__ double load_zero_filled(E* buf, const PlanDev<E>& P, const E* __restrict__ v,
+__device__ double load_zero_filled(const Grp& g, E* buf, const PlanDev<E>& P, const E* __restrict__ v,
                                    typename FT<E>::R scl) {
   double s = 0.0;
-  for (int pos = threadIdx.x; pos < P.N; pos += blockDim.x) {
+  for (int pos = g.tid; pos < P.N; pos += g.n) {
     const int m = __ldg(P.slot + pos);
     E e = zero<E>();
     if (m >= 0) {
@@ -74,70 +80,114 @@ __device__ double load_zero_filled(E* buf, const PlanDev<E>& P, const E* __restr
     }
     buf[swz<E>(pos)] = e;
   }
-  __syncthreads();
+  g.sync();
   return s;
 }
 
-// 1/sqrt(N) for N = 2^logN, exact to the working precision without FP64 math
-template <class R>
-__device__ __forceinline__ R inv_sqrt_pow2(int logN) {
-  const R r = (R)1 / (R)(1 << (logN >> 1));
-  return (logN & 1) ? r * (R)0.70710678118654752440 : r;
-}
+// First-pass loader of the forward synthesis: the zero-filled coefficient
+// vector x_Lambda, read from the support bitmap and the position ->
+// coefficient index map.  The first forward pass strides by N/16, so a warp
+// reads 32 consecutive positions (one bitmap word, broadcast).
+template <class E>
+struct SparseLoader {
+  const uint32_t* bits;
+  const uint16_t* kidx;
+  const E* xw;
+  __device__ __forceinline__ E operator()(int pos) const {
+    return in_bits(bits, pos) ? xw[kidx[pos]] : zero<E>();
+  }
+};
 
-// h = A^H zf_Omega(v): one adjoint transform.  buf ends in natural order.
+// Last-pass sink of a correlation: running arg-max of |h(j)|^2 over j not
+// flagged in `bits` (NULL: none), lowest j on ties; optionally stores h.  The
+// last adjoint pass strides by N/16, so a warp's outputs are consecutive.
+template <class E>
+struct ArgmaxSink {
+  using V = typename NormT<E>::V;
+  const uint32_t* bits;
+  E* h_out;
+  V bv;
+  int bj;
+  __device__ __forceinline__ void operator()(int j, const E& h) {
+    if (h_out) h_out[j] = h;
+    const V v = (bits && in_bits(bits, j)) ? (V)-1 : (V)norm2(h);
+    if (better(v, j, bv, bj)) { bv = v; bj = j; }
+  }
+};
+
+// h = A^H zf_Omega(v) by one adjoint transform, fused with the arg-max of
+// step 3 (no exclusions) and an optional store of h; returns the arg-max
+// (to every thread of g) and, with NORM, this thread's share of sum |v_m|^2
+// in *norm (FP64; reduce it over g).
 template <class E, bool DFT, bool NORM = false>
-__device__ double correlate_transform(E* buf, const PlanDev<E>& P, const E* __restrict__ v) {
+__device__ int correlate_transform(const Grp& g, E* buf, const PlanDev<E>& P, const E* __restrict__ v, E* h_out,
+                                   double* norm, typename NormT<E>::V* rv, int* rj) {
   using R = typename FT<E>::R;
-  const double s = load_zero_filled<E, NORM>(buf, P, v, inv_sqrt_pow2<R>(P.logN));
-  transform_adjoint<E, DFT>(buf, P);
-  return s;
+  using V = typename NormT<E>::V;
+  const double s = load_zero_filled<E, NORM>(g, buf, P, v, inv_sqrt_pow2<R>(P.logN));
+  ArgmaxSink<E> sk{nullptr, h_out, (V)-1, 0x7fffffff};
+  if constexpr (DFT) dft_adjoint(g, buf, P.logN, P.tw, NoLoad{}, sk);
+  else wht(g, buf, P.logN, NoLoad{}, sk);
+  if (norm) *norm = s;
+  return group_argmax(g, sk.bv, sk.bj, rv, rj);
 }
 
-// h = A^H zf(y - S_Omega A x_Lambda) for s atoms (lam[k], x[k]): a forward
-// transform of the zero-filled coefficients, the masked residual on Omega,
-// one adjoint transform.  buf ends in natural order.
+// h = A^H zf(y - S_Omega A x_Lambda) for the support in (bits, kidx, xw):
+// forward transform of the zero-filled coefficients (the first pass
+// assembles them from the support), the masked residual on Omega, one
+// adjoint transform whose last pass feeds the arg-max over j not in Lambda.
+// Returns the arg-max to every thread of g.
 template <class E, bool DFT>
-__device__ void correlate_residual(E* buf, const PlanDev<E>& P, const E* __restrict__ y,
-                                   const int* lam, const E* xw, int s) {
+__device__ int correlate_residual(const Grp& g, E* buf, const PlanDev<E>& P, const E* __restrict__ y,
+                                  const uint32_t* bits, const uint16_t* kidx, const E* xw,
+                                  typename NormT<E>::V* rv, int* rj) {
   using R = typename FT<E>::R;
+  using V = typename NormT<E>::V;
   const int N = P.N;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) buf[swz<E>(i)] = zero<E>();
-  __syncthreads();
-  for (int k = threadIdx.x; k < s; k += blockDim.x) buf[swz<E>(lam[k])] = xw[k];
-  __syncthreads();
-  transform_forward<E, DFT>(buf, P);
+  const SparseLoader<E> sl{bits, kidx, xw};
+  if constexpr (DFT) dft_forward(g, buf, P.logN, P.tw, sl, NoSink{});
+  else wht(g, buf, P.logN, sl, NoSink{});
   // buf holds F x (unnormalised).  Write N^{-1/2} y - N^{-1} F x on Omega and
   // zero elsewhere; the unnormalised adjoint then yields
   // N^{-1/2} F^H zf(y) - N^{-1} F^H S^T S F x = A^H zf(y - S A x).
   const R sy = inv_sqrt_pow2<R>(P.logN), sx = (R)1 / (R)N;
-  for (int pos = threadIdx.x; pos < N; pos += blockDim.x) {
+  for (int pos = g.tid; pos < N; pos += g.n) {
     const int m = __ldg(P.slot + pos);
     const int a = swz<E>(pos);
     buf[a] = m >= 0 ? sub(scale(y[m], sy), scale(buf[a], sx)) : zero<E>();
   }
-  __syncthreads();
-  transform_adjoint<E, DFT>(buf, P);
+  g.sync();
+  ArgmaxSink<E> sk{bits, nullptr, (V)-1, 0x7fffffff};
+  if constexpr (DFT) dft_adjoint(g, buf, P.logN, P.tw, NoLoad{}, sk);
+  else wht(g, buf, P.logN, NoLoad{}, sk);
+  return group_argmax(g, sk.bv, sk.bj, rv, rj);
+}
+
+// Whether the fast correlation stores c twice over (DFT, when 2N elements
+// fit in 128 KB of shared memory).
+template <class E>
+__host__ __device__ inline bool kernel_doubled(int N) {
+  return FT<E>::C && 2 * (size_t)N * sizeof(E) <= (size_t)128 * 1024;
 }
 
 // Load c into shared memory for the fast correlation.  With `doubled` (DFT
 // only) c is stored twice over so that c[(j - l) mod N + T e] is read at an
 // immediate offset without a wrap test; otherwise the index is masked.
 template <class E, bool DFT>
-__device__ void load_kernel_vector(E* cb, const PlanDev<E>& P, bool doubled) {
+__device__ void load_kernel_vector(const Grp& g, E* cb, const PlanDev<E>& P, bool doubled) {
   const int n = (DFT && doubled) ? 2 * P.N : P.N;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) cb[i] = __ldg(P.c + (i & (P.N - 1)));
-  __syncthreads();
+  for (int i = g.tid; i < n; i += g.n) cb[i] = __ldg(P.c + (i & (P.N - 1)));
+  g.sync();
 }
 
 // One chunk of CH outputs per thread: j = j0 + T e, e < CH.
 template <class E, bool DFT, bool DBL, int CH>
-__device__ __forceinline__ void fast_chunks(const E* cb, const E* h0, const int* lam,
-                                            const E* xw, int s, int N, const uint32_t* bits,
-                                            E* __restrict__ h_out, typename NormT<E>::V& bv, int& bj) {
+__device__ __forceinline__ void fast_chunks(const Grp& g, const E* cb, const E* h0, const int* lam,
+                                            const E* xw, int s, int N, const uint32_t* bits, E* h_out,
+                                            typename NormT<E>::V& bv, int& bj) {
   using V = typename NormT<E>::V;
-  const int T = blockDim.x;
-  for (int j0 = threadIdx.x; j0 < N; j0 += T * CH) {
+  const int T = g.n;
+  for (int j0 = g.tid; j0 < N; j0 += T * CH) {
     E acc[CH];
 #pragma unroll
     for (int e = 0; e < CH; ++e) acc[e] = h0[j0 + T * e];
@@ -167,36 +217,28 @@ __device__ __forceinline__ void fast_chunks(const E* cb, const E* h0, const int*
 }
 
 template <class E, bool DFT, bool DBL>
-__device__ __forceinline__ void fast_dispatch(const E* cb, const E* h0, const int* lam, const E* xw, int s, int N,
-                                              const uint32_t* bits, E* __restrict__ h_out,
+__device__ __forceinline__ void fast_dispatch(const Grp& g, const E* cb, const E* h0, const int* lam, const E* xw,
+                                              int s, int N, const uint32_t* bits, E* h_out,
                                               typename NormT<E>::V& bv, int& bj) {
-  const int per = N / blockDim.x;  // outputs per thread (power of two, or 0 when N < T)
-  if (per >= 8) fast_chunks<E, DFT, DBL, 8>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
-  else if (per >= 4) fast_chunks<E, DFT, DBL, 4>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
-  else if (per >= 2) fast_chunks<E, DFT, DBL, 2>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
-  else fast_chunks<E, DFT, DBL, 1>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  const int per = N / g.n;  // outputs per thread (power of two, or 0 when N < T)
+  if (per >= 8) fast_chunks<E, DFT, DBL, 8>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  else if (per >= 4) fast_chunks<E, DFT, DBL, 4>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  else if (per >= 2) fast_chunks<E, DFT, DBL, 2>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  else fast_chunks<E, DFT, DBL, 1>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
 }
 
 // h(j) = h0(j) - sum_{k<s} x_k c(j (-) lam_k) for all j (Eq. kernelsumOMP),
 // then the arg-max over j not in `bits`.  cb is c in shared memory, stored
 // twice over when `doubled` (DFT).
 template <class E, bool DFT>
-__device__ int correlate_fast(const E* cb, const E* h0, const int* lam, const E* xw,
-                              int s, int N, const uint32_t* bits, E* __restrict__ h_out,
-                              typename NormT<E>::V* rv, int* rj, bool doubled) {
+__device__ int correlate_fast(const Grp& g, const E* cb, const E* h0, const int* lam, const E* xw, int s, int N,
+                              const uint32_t* bits, E* h_out, typename NormT<E>::V* rv, int* rj, bool doubled) {
   using V = typename NormT<E>::V;
   V bv = (V)-1;
   int bj = 0x7fffffff;
-  if (DFT && doubled) fast_dispatch<E, DFT, true>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
-  else fast_dispatch<E, DFT, false>(cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
-  return block_argmax(bv, bj, rv, rj);
-}
-
-// Whether the fast correlation stores c twice over (DFT, when 2N elements
-// fit in 128 KB of shared memory).
-template <class E>
-__host__ __device__ inline bool kernel_doubled(int N) {
-  return FT<E>::C && 2 * (size_t)N * sizeof(E) <= (size_t)128 * 1024;
+  if (DFT && doubled) fast_dispatch<E, DFT, true>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  else fast_dispatch<E, DFT, false>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  return group_argmax(g, bv, bj, rv, rj);
 }
 
 // ------------------------------------------------------------------------
@@ -208,45 +250,34 @@ __host__ __device__ inline bool kernel_doubled(int N) {
 //   u = B g,  d^2 = c(0) - ||u||^2,  zeta = (b_p - u^H z) / d,
 //   row p of B = [-(u^H B) / d, 1 / d],   x += zeta * conj(row p of B),
 //   ||r||^2 -= |zeta|^2.
-// Both products with B are spread over every thread with rows (columns)
-// paired i <-> p-1-i so that all lanes carry equal work.
-template <class W>
-struct LsSmem {
-  W* z;     // [Kmax]
-  W* x;     // [Kmax]
-  W* g;     // [Kmax]  Gram column, then u
-  W* part;  // [2T]    partial sums
-};
-
 __device__ __forceinline__ int pidx(int i) { return (i * (i + 1)) >> 1; }
 
 // Layout of the paired, chunked triangular products: row (column) pairs
-// i <-> p-1-i over lanes, the concatenated pair split into `chunks` slices
-// over warps, at most T / (2 lanes) of them so that the partial sums fit in
-// max(T, p) elements (4 warps, one per SM sub-partition, when p <= 64).  When
-// there are more pairs than threads, each thread walks pairs with stride T.
+// i <-> p-1-i over lanes, so that every lane carries p + 1 terms; the
+// concatenated pair split into `chunks` slices over the group's warps (in a
+// 4-warp group, one warp per SM sub-partition carries the FP64 work).
+// Partial sums take chunks * p <= max(2 n, p) elements.  With more pairs than
+// threads each thread walks pairs with stride n and chunks = 1.
 struct PairSplit {
   int P2, chunks, pair, chunk, stride;
-  __device__ PairSplit(int p) {
+  __device__ PairSplit(const Grp& g, int p) {
     P2 = (p + 1) >> 1;
-    const int T = blockDim.x;
     int lanes = ((P2 + 31) >> 5) << 5;
     if (lanes == 0) lanes = 32;
-    chunks = T / (2 * lanes);
-    if (chunks < 1) chunks = 1;
-    stride = lanes <= T ? lanes : T;
-    pair = threadIdx.x % stride;
-    chunk = threadIdx.x / stride;
+    chunks = lanes <= g.n ? g.n / lanes : 1;
+    stride = lanes <= g.n ? lanes : g.n;
+    pair = g.tid % stride;
+    chunk = g.tid / stride;
   }
 };
 
-// u_i = sum_{k<=i} B[i][k] g_k, i < p; result overwrites g.  part holds
-// max(T, p) elements.  B is read with plain loads: it is written by the
+// u_i = sum_{k<=i} B[i][k] g_k, i < p; result overwrites gv.  part holds
+// max(2 n, p) elements.  B is read with plain loads: it is written by the
 // same kernel.
 template <class W>
-__device__ void tri_matvec(const W* B, W* g, W* part, int p) {
+__device__ void tri_matvec(const Grp& grp, const W* B, W* gv, W* part, int p) {
   if (p == 0) return;
-  PairSplit ps(p);
+  PairSplit ps(grp, p);
   if (ps.chunk < ps.chunks) {
     for (int pr = ps.pair; pr < ps.P2; pr += ps.stride) {
       const int ra = pr, rb = p - 1 - pr;
@@ -256,12 +287,12 @@ __device__ void tri_matvec(const W* B, W* g, W* part, int p) {
       // falls in: the row switch is a register move, not a second FMA path.
       W acc = W{}, first = W{};
       const W* Bb = B + pidx(rb) - la;
-      const W* gb = g - la;
+      const W* gb = gv - la;
       const W* Ba = B + pidx(ra);
       for (int q = q0; q < q1; ++q) {
         const bool second = q >= la;
         if (q == la) { first = acc; acc = W{}; }
-        acc = fmav(acc, second ? Bb[q] : Ba[q], second ? gb[q] : g[q]);
+        acc = fmav(acc, second ? Bb[q] : Ba[q], second ? gb[q] : gv[q]);
       }
       const bool ended_in_b = q1 > la;
       const W pa = ended_in_b ? (q0 < la ? first : W{}) : acc;
@@ -270,21 +301,21 @@ __device__ void tri_matvec(const W* B, W* g, W* part, int p) {
       if (rb != ra) part[ps.chunk * p + rb] = pb;
     }
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+  grp.sync();
+  for (int i = grp.tid; i < p; i += grp.n) {
     W s = part[i];
     for (int c = 1; c < ps.chunks; ++c) s = add(s, part[c * p + i]);
-    g[i] = s;
+    gv[i] = s;
   }
-  __syncthreads();
+  grp.sync();
 }
 
 // w_k = scl * sum_{i=k}^{p-1} conj(u_i) B[i][k], k < p, written to row p of
 // B and to part[0..p).
 template <class W>
-__device__ void tri_vecmat_row(W* B, const W* u, W* part, int p, double scl) {
+__device__ void tri_vecmat_row(const Grp& grp, W* B, const W* u, W* part, int p, double scl) {
   if (p == 0) return;
-  PairSplit ps(p);
+  PairSplit ps(grp, p);
   if (ps.chunk < ps.chunks) {
     for (int pr = ps.pair; pr < ps.P2; pr += ps.stride) {
       const int ka = pr, kb = p - 1 - pr;
@@ -304,16 +335,16 @@ __device__ void tri_vecmat_row(W* B, const W* u, W* part, int p, double scl) {
       if (kb != ka) part[ps.chunk * p + kb] = pb;
     }
   }
-  __syncthreads();
+  grp.sync();
   // part[k] (chunk 0) is only ever read by the thread that owns column k
-  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+  for (int k = grp.tid; k < p; k += grp.n) {
     W s = part[k];
     for (int c = 1; c < ps.chunks; ++c) s = add(s, part[c * p + k]);
     s = scale(s, scl);
     part[k] = s;
     B[pidx(p) + k] = s;
   }
-  __syncthreads();
+  grp.sync();
 }
 
 }  // namespace csf

@@ -214,6 +214,31 @@ __device__ __forceinline__ void wht_reg(E (&v)[R]) {
   if constexpr (R > 1) wht_stage<R, R / 2>(v);
 }
 
+// ------------------------------------------------------------ thread groups
+// A group of whole warps of one CTA working on one task: `tid` is the thread
+// index within the group, `n` its size, `bar` the hardware barrier it
+// synchronises on (0 = the CTA-wide barrier when the group is the whole CTA).
+// The compiler does not know that the inline named barrier is a barrier, so
+// it would not reconverge a warp whose lanes took different paths before it:
+// __syncwarp() reconverges the warp first, and the non-aligned form counts
+// every thread's arrival on its own.
+struct Grp {
+  int tid, n, bar;
+  __device__ __forceinline__ void sync() const {
+    if (bar == 0) {
+      __syncthreads();
+    } else {
+      __syncwarp();
+      asm volatile("barrier.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
+    }
+  }
+  __device__ __forceinline__ int lane() const { return tid & 31; }
+  __device__ __forceinline__ int warp() const { return tid >> 5; }
+  __device__ __forceinline__ int nwarps() const { return n >> 5; }
+};
+
+__device__ __forceinline__ Grp whole_block() { return Grp{(int)threadIdx.x, (int)blockDim.x, 0}; }
+
 // --------------------------------------------------------------- reductions
 template <class V>
 __device__ __forceinline__ bool better(V av, int aj, V bv, int bj) {
@@ -230,23 +255,24 @@ __device__ __forceinline__ void warp_argmax(V& v, int& j) {
   }
 }
 
-// Block-wide arg-max of (v, j): largest v, smallest j among equal v.  Entries
-// with v < 0 are "no candidate".  Returns j (or -1) to every thread.
+// Group-wide arg-max of (v, j): largest v, smallest j among equal v.  Entries
+// with v < 0 are "no candidate".  Returns j (or -1) to every thread of g.
+// rv, rj: 34 entries of group-private shared memory.
 template <class V>
-__device__ int block_argmax(V v, int j, V* rv, int* rj) {
+__device__ int group_argmax(const Grp& g, V v, int j, V* rv, int* rj) {
   warp_argmax(v, j);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int lane = g.lane(), w = g.warp(), nw = g.nwarps();
   if (lane == 0) { rv[w] = v; rj[w] = j; }
-  __syncthreads();
+  g.sync();
   if (w == 0) {
     V vv = lane < nw ? rv[lane] : (V)-1;
     int jj = lane < nw ? rj[lane] : 0x7fffffff;
     warp_argmax(vv, jj);
     if (lane == 0) { rj[32] = vv < (V)0 ? -1 : jj; }
   }
-  __syncthreads();
+  g.sync();
   const int r = rj[32];
-  __syncthreads();
+  g.sync();
   return r;
 }
 
@@ -256,17 +282,18 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-wide sums of up to 4 doubles; every thread gets the totals.
+// Group-wide sums of NV doubles; every thread of g gets the totals.
+// red: 32*NV + NV group-private doubles.
 template <int NV>
-__device__ void block_sum(double (&v)[NV], double* red /* >= 32*NV + NV */) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+__device__ void group_sum(const Grp& g, double (&v)[NV], double* red) {
+  const int lane = g.lane(), w = g.warp(), nw = g.nwarps();
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
   if (lane == 0) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) red[w * NV + i] = v[i];
   }
-  __syncthreads();
+  g.sync();
   if (w == 0) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
@@ -275,10 +302,10 @@ __device__ void block_sum(double (&v)[NV], double* red /* >= 32*NV + NV */) {
       if (lane == 0) red[32 * NV + i] = t;
     }
   }
-  __syncthreads();
+  g.sync();
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = red[32 * NV + i];
-  __syncthreads();
+  g.sync();
 }
 
 }  // namespace csf

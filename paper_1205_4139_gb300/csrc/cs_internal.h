@@ -19,7 +19,11 @@ struct PlanView {
   const void* tw32;   // float2 [N]  (DFT, FP32)
   const void* c64;    // double / double2 [N]
   const void* c32;    // float / float2 [N] (FP32)
+  int* status;        // device status word (kernel-detected errors), owned by the plan
 };
+
+// Bits of the device status word.
+constexpr int kStatusPhaseBound = 1;  // the OMP kernel's phase loop hit its bound
 
 struct OmpLaunch {
   const void* y;

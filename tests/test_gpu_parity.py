@@ -167,6 +167,7 @@ def test_omp_wht_fp64_single(path):
     inst = synth.make_batch(**synth.CONFIG_WHT_FP64_SINGLE)
     plan = binding.Plan(inst["N"], inst["omega"], "wht", "fp64")
     res = plan.omp(torch.from_numpy(inst["Y"]).cuda(), inst["K"], path=path)
+    assert plan.device_error() == 0
     check_omp(inst, res, "fp64", True)
     # exact recovery of the drawn signal
     x, supp, iters, _ = (t.cpu().numpy() for t in res)
@@ -179,6 +180,7 @@ def test_omp_small_batches(kind, prec, path):
     inst = synth.make_batch(kind, 512, 160, 12, 5, snr_db=None, prec=prec, seed=21)
     plan = binding.Plan(512, inst["omega"], kind, prec)
     res = plan.omp(torch.from_numpy(inst["Y"]).cuda(), 12, path=path)
+    assert plan.device_error() == 0
     check_omp(inst, res, prec, True)
 
 
@@ -191,6 +193,7 @@ def test_omp_dft_c64_noisy_batch(path):
     inst = synth.make_batch(**cfg)
     plan = binding.Plan(inst["N"], inst["omega"], "dft", "fp32")
     res = plan.omp(torch.from_numpy(inst["Y"]).cuda(), inst["K"], path=path)
+    assert plan.device_error() == 0
     check_omp(inst, res, "fp32", False)
 
 
