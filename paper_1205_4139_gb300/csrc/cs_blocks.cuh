@@ -274,8 +274,14 @@ struct PairSplit {
 // u_i = sum_{k<=i} B[i][k] g_k, i < p; result overwrites gv.  part holds
 // max(2 n, p) elements.  B is read with plain loads: it is written by the
 // same kernel.
+// u_i = sum_{k<=i} B[i][k] g_k, i < p; result overwrites gv.  part holds
+// max(2 n, p) elements.  B is read with plain loads: it is written by the
+// same kernel.  When `terms` is given, the thread that finishes u_k also
+// writes the FP64 terms |u_k|^2 and conj(u_k) z_k there (3 doubles per k),
+// for the caller's reductions.
 template <class W>
-__device__ void tri_matvec(const Grp& grp, const W* B, W* gv, W* part, int p) {
+__device__ void tri_matvec(const Grp& grp, const W* B, W* gv, W* part, int p, const W* z = nullptr,
+                           double* terms = nullptr) {
   if (p == 0) return;
   PairSplit ps(grp, p);
   if (ps.chunk < ps.chunks) {
@@ -306,6 +312,12 @@ __device__ void tri_matvec(const Grp& grp, const W* B, W* gv, W* part, int p) {
     W s = part[i];
     for (int c = 1; c < ps.chunks; ++c) s = add(s, part[c * p + i]);
     gv[i] = s;
+    if (terms) {
+      const W t = cmul(s, z[i]);
+      terms[3 * i] = norm2(s);
+      terms[3 * i + 1] = re(t);
+      terms[3 * i + 2] = im(t);
+    }
   }
   grp.sync();
 }

@@ -66,7 +66,8 @@ __host__ __device__ inline OmpLayout<E> omp_layout(int N, int K, int path) {
   using V = typename NormT<E>::V;
   OmpLayout<E> L;
   const int Kc = K > 0 ? K : 1;
-  const int npart = 2 * kLThreads > Kc ? 2 * kLThreads : Kc;
+  // chunk partials (max(2 n, K) elements), then 3 doubles per k of terms
+  const int npart = (2 * kLThreads > Kc ? 2 * kLThreads : Kc) + (3 * Kc * (int)sizeof(double) + (int)sizeof(W) - 1) / (int)sizeof(W);
   // per-slot block, offsets relative to the slot base
   size_t o = 0;
   L.z = o;    o = a16(o + (size_t)Kc * sizeof(W));
@@ -227,27 +228,33 @@ __device__ void ls_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const S
     v.g[k] = a.P.c64[d];                                  // G(lambda_k, lambda)
   }
   g.sync();
-  tri_matvec(g, v.B, v.g, v.part, p);                    // g <- u = B g
-  // Scalar FP64 work on one warp: an FP64 warp instruction costs the same
-  // whatever its active lanes, so the other warps skip it.
-  if (g.tid < 32) {
+  // g <- u = B g; the finishing threads leave |u_k|^2 and conj(u_k) z_k in
+  // `terms`, placed after the chunk partials of the same buffer
+  double* terms = (double*)(v.part + (2 * kLThreads > K ? 2 * kLThreads : K));
+  tri_matvec(g, v.B, v.g, v.part, p, v.z, terms);
+  // d^2 and u^H z: one warp adds the terms, one thread runs the scalar FP64
+  // work (a warp FP64 instruction costs the same whatever its active lanes,
+  // so the other warps wait at the barrier instead of repeating it).  It is
+  // the group's last warp: the first warps already carry the combines of the
+  // low k.
+  const int lw = g.nwarps() - 1;
+  if (g.warp() == lw) {
     double an = 0.0, ar = 0.0, ai = 0.0;
-    for (int k = g.tid; k < p; k += 32) {
-      an += norm2(v.g[k]);
-      const W t = cmul(v.g[k], v.z[k]);
-      ar += re(t);
-      ai += im(t);
+    for (int k = g.lane(); k < p; k += 32) {
+      an += terms[3 * k];
+      ar += terms[3 * k + 1];
+      ai += terms[3 * k + 2];
     }
     an = warp_sum(an);
     ar = warp_sum(ar);
     if constexpr (DFT) ai = warp_sum(ai);
-    if (g.tid == 0) {
+    if (g.lane() == 0) {
       const double d2 = c0 - an;
       int st = 0;
       if (!(d2 > dep)) {
         st = 1;                                          // column dependent on Lambda
       } else {
-        const double invd = 1.0 / sqrt(d2);
+        const double invd = rsqrt(d2);
         const W bp = to_w(v.h0[l]);                       // (Phi^H y)(lambda)
         const W zeta = scale(sub(bp, make_w<W>(ar, ai)), invd);
         const double r2 = S.rn2 - norm2(zeta);
