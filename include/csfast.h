@@ -69,11 +69,14 @@ typedef enum { CS_PATH_FAST = 0, CS_PATH_CONV = 1, CS_PATH_HYBRID = 2 } cs_path;
  * the tolerance).  A zero measurement halts before the first iteration; a
  * selected column whose Cholesky pivot is <= 1e-10 * M/N (numerically
  * dependent on the support) ends the run without being added.
- * t_switch < 0 selects the plan's default switch point (cs_plan_info). */
+ * t_switch < 0 selects the plan's default switch point (cs_plan_info).
+ * max_iter bounds the iterations of cs_sp / cs_cosamp (<= 0: K for SP, 50 for
+ * CoSaMP); cs_omp ignores it (its bound is K). */
 typedef struct {
   double rel_tol;
   int32_t path;
   int32_t t_switch;
+  int32_t max_iter;
 } cs_halt;
 
 /* Build a plan for Phi = S_Omega A (Sec. I).  Computes on the device the
@@ -138,6 +141,30 @@ cs_status cs_correlate_fast(cs_plan_t plan, const void* h0_dev, const int32_t* s
 cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
                  void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev,
                  void* stream);
+
+/* Subspace pursuit and CoSaMP on `batch` measurements sharing the plan's
+ * Omega, one CTA per instance.  The paper applies its correlation to these
+ * algorithms (Sec. I) and reports the cost of a fast CoSaMP (Sec. IV) without
+ * defining them; they take their standard forms:
+ *   SP:     T = top_K(Phi^H y), x = LS on T; each iteration T' = T + top_K of
+ *           |Phi^H r| over j not in T, b = LS on T', T_new = K largest |b|,
+ *           x_new = LS on T_new;
+ *   CoSaMP: x = 0; each iteration T = top_2K(|Phi^H r|) + supp(x), b = LS on
+ *           T, x_new = b kept on its K largest |b|;
+ * both stop, keeping the previous iterate, when the residual norm does not
+ * decrease, and stop when ||r|| < rel_tol ||y|| or after max_iter iterations.
+ * top_k breaks ties toward the lower index.  halt->path selects the
+ * correlation: CS_PATH_FAST = kernel sums over the estimate's support
+ * (Eq. kernelsum), CS_PATH_CONV = transforms, CS_PATH_HYBRID = kernel sums
+ * when K <= t_switch.  Least squares are FP64 (normal equations, Cholesky
+ * factor from c).  Outputs per instance: x_dev FP64 [K] and supp_dev [K] on
+ * the final support in ascending column order (-1 / 0 past its size),
+ * iters_dev (iterations run), resnorm_dev (||r|| / ||y||).
+ * Limits: 1 <= K, 2K <= M (SP), 3K <= M (CoSaMP), K <= 128. */
+cs_status cs_sp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
+                void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev, void* stream);
+cs_status cs_cosamp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
+                    void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev, void* stream);
 
 /* cs_omp without any allocation by the library: the paper has no
  * counterpart; this exists for callers that must not allocate device memory

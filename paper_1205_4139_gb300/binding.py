@@ -23,7 +23,8 @@ PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 
 # Every function include/csfast.h declares.
 EXPORTS = ["cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
-           "cs_correlate_fast", "cs_omp", "cs_omp_noalloc", "cs_status_string", "cs_last_error"]
+           "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_status_string",
+           "cs_last_error"]
 
 
 class CsError(RuntimeError):
@@ -31,7 +32,8 @@ class CsError(RuntimeError):
 
 
 class Halt(ctypes.Structure):
-    _fields_ = [("rel_tol", ctypes.c_double), ("path", ctypes.c_int32), ("t_switch", ctypes.c_int32)]
+    _fields_ = [("rel_tol", ctypes.c_double), ("path", ctypes.c_int32), ("t_switch", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32)]
 
 
 _lib = None
@@ -57,8 +59,10 @@ def load(path: str = LIB_PATH):
     L.cs_correlate_fast.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, vp]
     L.cs_omp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_omp_noalloc.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
+    L.cs_sp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
+    L.cs_cosamp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     for f in ("cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
-              "cs_correlate_fast", "cs_omp", "cs_omp_noalloc"):
+              "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc"):
         getattr(L, f).restype = ctypes.c_int
     L.cs_status_string.argtypes = [ctypes.c_int]
     L.cs_status_string.restype = ctypes.c_char_p
@@ -169,8 +173,8 @@ class Plan:
 
     def omp_into(self, y, K: int, x, supp, iters, resnorm, rel_tol: float = 1e-6, path: str = "hybrid",
                  t_switch: int = -1, stream=None):
-        """cs_omp into caller-provided outputs (no allocation)."""
-        hl = Halt(rel_tol, PATHS[path], t_switch)
+        """cs_omp into outputs the caller provides."""
+        hl = Halt(rel_tol, PATHS[path], t_switch, 0)
         _check(load().cs_omp(self._h, _ptr(y), y.shape[0], K, ctypes.byref(hl), _ptr(x), _ptr(supp), _ptr(iters),
                              _ptr(resnorm), _stream(stream)))
 
@@ -184,4 +188,25 @@ class Plan:
         iters = torch.empty(B, dtype=torch.int32, device="cuda")
         res = torch.empty(B, dtype=torch.float64, device="cuda")
         self.omp_into(y, K, x, supp, iters, res, rel_tol, path, t_switch, stream)
+        return x, supp, iters, res
+
+    def pursuit_into(self, algo: str, y, K: int, x, supp, iters, resnorm, rel_tol: float = 1e-6,
+                     path: str = "fast", max_iter: int = 0, t_switch: int = -1, stream=None):
+        """cs_sp (algo 'sp') or cs_cosamp (algo 'cosamp') into outputs the caller provides."""
+        hl = Halt(rel_tol, PATHS[path], t_switch, max_iter)
+        fn = load().cs_sp if algo == "sp" else load().cs_cosamp
+        _check(fn(self._h, _ptr(y), y.shape[0], K, ctypes.byref(hl), _ptr(x), _ptr(supp), _ptr(iters),
+                  _ptr(resnorm), _stream(stream)))
+
+    def pursuit(self, algo: str, y, K: int, rel_tol: float = 1e-6, path: str = "fast", max_iter: int = 0,
+                stream=None):
+        """Subspace pursuit or CoSaMP on a (batch, M) tensor; returns x (FP64), supp, iters, resnorm."""
+        import torch
+        self._want(y, self.M)
+        B = y.shape[0]
+        x = torch.empty(B, K, dtype=ls_dtype(self.kind), device="cuda")
+        supp = torch.empty(B, K, dtype=torch.int32, device="cuda")
+        iters = torch.empty(B, dtype=torch.int32, device="cuda")
+        res = torch.empty(B, dtype=torch.float64, device="cuda")
+        self.pursuit_into(algo, y, K, x, supp, iters, res, rel_tol, path, max_iter, stream=stream)
         return x, supp, iters, res

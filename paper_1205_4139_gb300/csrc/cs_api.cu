@@ -227,7 +227,7 @@ extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, in
   if (!plan || batch < 0 || K < 0) return CS_ERR_INVALID;
   if (K > plan->v.M) return CS_ERR_INVALID;
   if (K > kMaxK) return CS_ERR_UNSUPPORTED;
-  cs_halt h = {1e-6, CS_PATH_HYBRID, -1};
+  cs_halt h = {1e-6, CS_PATH_HYBRID, -1, 0};
   if (halt) h = *halt;
   if (!(h.rel_tol >= 0.0) || !std::isfinite(h.rel_tol)) return CS_ERR_INVALID;
   if (h.path != CS_PATH_FAST && h.path != CS_PATH_CONV && h.path != CS_PATH_HYBRID) return CS_ERR_INVALID;
@@ -261,4 +261,57 @@ extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, in
   a.res_out = resnorm_dev;
   CS_CUDA(launch_omp(plan->v, a, plan->ws, grid, st), "omp kernel");
   return CS_OK;
+}
+
+static cs_status pursuit_call(int algo, cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K,
+                              const cs_halt* halt, void* x_dev, int32_t* supp_dev, int32_t* iters_dev,
+                              double* resnorm_dev, void* stream) {
+  if (!plan || batch < 0 || K < 1) return CS_ERR_INVALID;
+  if ((algo == 0 ? 2 : 3) * (int64_t)K > plan->v.M) return CS_ERR_INVALID;
+  if (K > 128) return CS_ERR_UNSUPPORTED;
+  cs_halt h = {1e-6, CS_PATH_HYBRID, -1, 0};
+  if (halt) h = *halt;
+  if (!(h.rel_tol >= 0.0) || !std::isfinite(h.rel_tol)) return CS_ERR_INVALID;
+  if (h.path != CS_PATH_FAST && h.path != CS_PATH_CONV && h.path != CS_PATH_HYBRID) return CS_ERR_INVALID;
+  if (batch == 0) return CS_OK;
+  if (!supp_dev || !y_dev) return CS_ERR_INVALID;
+  const int t_switch = h.t_switch < 0 ? plan->t_switch_default : h.t_switch;
+  const int fast = h.path == CS_PATH_FAST || (h.path == CS_PATH_HYBRID && K <= t_switch);
+  cudaStream_t st = (cudaStream_t)stream;
+  int err = 0;
+  const int grid = pursuit_grid(plan->v, K, algo, fast, batch, &err);
+  if (err) return cuda_fail((cudaError_t)err, "pursuit configuration");
+  const size_t need = pursuit_workspace_bytes(plan->v, K, algo, grid);
+  if (need > plan->ws_bytes) {
+    if (plan->ws) CS_CUDA(cudaFreeAsync(plan->ws, st), "cudaFreeAsync workspace");
+    plan->ws = nullptr;
+    plan->ws_bytes = 0;
+    CS_CUDA(cudaMallocAsync(&plan->ws, need, st), "cudaMallocAsync workspace");
+    plan->ws_bytes = need;
+  }
+  PursuitLaunch a;
+  a.y = y_dev;
+  a.batch = batch;
+  a.K = K;
+  a.algo = algo;
+  a.max_iter = h.max_iter > 0 ? h.max_iter : (algo == 0 ? K : 50);
+  a.fast = fast;
+  a.rel_tol = h.rel_tol;
+  a.x_out = x_dev;
+  a.supp_out = supp_dev;
+  a.iters_out = iters_dev;
+  a.res_out = resnorm_dev;
+  CS_CUDA(launch_pursuit(plan->v, a, plan->ws, grid, st), "pursuit kernel");
+  return CS_OK;
+}
+
+extern "C" cs_status cs_sp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
+                           void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev, void* stream) {
+  return pursuit_call(0, plan, y_dev, batch, K, halt, x_dev, supp_dev, iters_dev, resnorm_dev, stream);
+}
+
+extern "C" cs_status cs_cosamp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
+                               void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev,
+                               void* stream) {
+  return pursuit_call(1, plan, y_dev, batch, K, halt, x_dev, supp_dev, iters_dev, resnorm_dev, stream);
 }

@@ -41,6 +41,20 @@ inline PlanDev<E> plan_dev(const PlanView& P) {
 // |h|^2 type used for identification: the working precision.
 template <class E> struct NormT { using V = typename FT<E>::R; };
 
+// Selection keys: unsigned integers that order like |h|^2 (the bit pattern of
+// a non-negative IEEE number orders like the number), with the top bit set
+// for candidates and 0 for excluded positions, in the working precision's
+// width (32 bits for FP32, 64 for FP64).
+template <class E> struct KeyT;
+template <> struct KeyT<float> { using U = uint32_t; };
+template <> struct KeyT<float2> { using U = uint32_t; };
+template <> struct KeyT<double> { using U = unsigned long long; };
+template <> struct KeyT<double2> { using U = unsigned long long; };
+__device__ __forceinline__ uint32_t sel_key(float v) { return __float_as_uint(v) | 0x80000000u; }
+__device__ __forceinline__ unsigned long long sel_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) | 0x8000000000000000ull;
+}
+
 // Unnormalised transform of the kind: DFT uses F^H (adjoint chain) for the
 // correlation and F (forward chain) for the synthesis; WHT uses H for both.
 template <class E, bool DFT>
@@ -108,9 +122,12 @@ struct ArgmaxSink {
   E* h_out;
   V bv;
   int bj;
+  typename KeyT<E>::U* keys;  // selection keys (nullable)
   __device__ __forceinline__ void operator()(int j, const E& h) {
     if (h_out) h_out[j] = h;
-    const V v = (bits && in_bits(bits, j)) ? (V)-1 : (V)norm2(h);
+    const bool ex = bits && in_bits(bits, j);
+    const V v = ex ? (V)-1 : (V)norm2(h);
+    if (keys) keys[j] = ex ? 0 : sel_key(v);
     if (better(v, j, bv, bj)) { bv = v; bj = j; }
   }
 };
@@ -125,7 +142,7 @@ __device__ int correlate_transform(const Grp& g, E* buf, const PlanDev<E>& P, co
   using R = typename FT<E>::R;
   using V = typename NormT<E>::V;
   const double s = load_zero_filled<E, NORM>(g, buf, P, v, inv_sqrt_pow2<R>(P.logN));
-  ArgmaxSink<E> sk{nullptr, h_out, (V)-1, 0x7fffffff};
+  ArgmaxSink<E> sk{nullptr, h_out, (V)-1, 0x7fffffff, nullptr};
   if constexpr (DFT) dft_adjoint(g, buf, P.logN, P.tw, NoLoad{}, sk);
   else wht(g, buf, P.logN, NoLoad{}, sk);
   if (norm) *norm = s;
@@ -140,7 +157,8 @@ __device__ int correlate_transform(const Grp& g, E* buf, const PlanDev<E>& P, co
 template <class E, bool DFT>
 __device__ int correlate_residual(const Grp& g, E* buf, const PlanDev<E>& P, const E* __restrict__ y,
                                   const uint32_t* bits, const uint16_t* kidx, const E* xw,
-                                  typename NormT<E>::V* rv, int* rj) {
+                                  typename NormT<E>::V* rv, int* rj, const uint32_t* excl = nullptr,
+                                  typename KeyT<E>::U* keys = nullptr) {
   using R = typename FT<E>::R;
   using V = typename NormT<E>::V;
   const int N = P.N;
@@ -157,7 +175,8 @@ __device__ int correlate_residual(const Grp& g, E* buf, const PlanDev<E>& P, con
     buf[a] = m >= 0 ? sub(scale(y[m], sy), scale(buf[a], sx)) : zero<E>();
   }
   g.sync();
-  ArgmaxSink<E> sk{bits, nullptr, (V)-1, 0x7fffffff};
+  // OMP excludes the support itself; the pursuits pass their own exclusion
+  ArgmaxSink<E> sk{keys ? excl : bits, nullptr, (V)-1, 0x7fffffff, keys};
   if constexpr (DFT) dft_adjoint(g, buf, P.logN, P.tw, NoLoad{}, sk);
   else wht(g, buf, P.logN, NoLoad{}, sk);
   return group_argmax(g, sk.bv, sk.bj, rv, rj);
@@ -184,7 +203,7 @@ __device__ void load_kernel_vector(const Grp& g, E* cb, const PlanDev<E>& P, boo
 template <class E, bool DFT, bool DBL, int CH>
 __device__ __forceinline__ void fast_chunks(const Grp& g, const E* cb, const E* h0, const int* lam,
                                             const E* xw, int s, int N, const uint32_t* bits, E* h_out,
-                                            typename NormT<E>::V& bv, int& bj) {
+                                            typename NormT<E>::V& bv, int& bj, typename KeyT<E>::U* keys) {
   using V = typename NormT<E>::V;
   const int T = g.n;
   for (int j0 = g.tid; j0 < N; j0 += T * CH) {
@@ -210,7 +229,9 @@ __device__ __forceinline__ void fast_chunks(const Grp& g, const E* cb, const E* 
     for (int e = 0; e < CH; ++e) {
       const int j = j0 + T * e;
       if (h_out) h_out[j] = acc[e];
-      const V v = (bits && in_bits(bits, j)) ? (V)-1 : (V)norm2(acc[e]);
+      const bool ex = bits && in_bits(bits, j);
+      const V v = ex ? (V)-1 : (V)norm2(acc[e]);
+      if (keys) keys[j] = ex ? 0 : sel_key(v);
       if (better(v, j, bv, bj)) { bv = v; bj = j; }
     }
   }
@@ -219,12 +240,12 @@ __device__ __forceinline__ void fast_chunks(const Grp& g, const E* cb, const E* 
 template <class E, bool DFT, bool DBL>
 __device__ __forceinline__ void fast_dispatch(const Grp& g, const E* cb, const E* h0, const int* lam, const E* xw,
                                               int s, int N, const uint32_t* bits, E* h_out,
-                                              typename NormT<E>::V& bv, int& bj) {
+                                              typename NormT<E>::V& bv, int& bj, typename KeyT<E>::U* keys) {
   const int per = N / g.n;  // outputs per thread (power of two, or 0 when N < T)
-  if (per >= 8) fast_chunks<E, DFT, DBL, 8>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
-  else if (per >= 4) fast_chunks<E, DFT, DBL, 4>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
-  else if (per >= 2) fast_chunks<E, DFT, DBL, 2>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
-  else fast_chunks<E, DFT, DBL, 1>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  if (per >= 8) fast_chunks<E, DFT, DBL, 8>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj, keys);
+  else if (per >= 4) fast_chunks<E, DFT, DBL, 4>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj, keys);
+  else if (per >= 2) fast_chunks<E, DFT, DBL, 2>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj, keys);
+  else fast_chunks<E, DFT, DBL, 1>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj, keys);
 }
 
 // h(j) = h0(j) - sum_{k<s} x_k c(j (-) lam_k) for all j (Eq. kernelsumOMP),
@@ -232,12 +253,13 @@ __device__ __forceinline__ void fast_dispatch(const Grp& g, const E* cb, const E
 // twice over when `doubled` (DFT).
 template <class E, bool DFT>
 __device__ int correlate_fast(const Grp& g, const E* cb, const E* h0, const int* lam, const E* xw, int s, int N,
-                              const uint32_t* bits, E* h_out, typename NormT<E>::V* rv, int* rj, bool doubled) {
+                              const uint32_t* bits, E* h_out, typename NormT<E>::V* rv, int* rj, bool doubled,
+                              typename KeyT<E>::U* keys = nullptr) {
   using V = typename NormT<E>::V;
   V bv = (V)-1;
   int bj = 0x7fffffff;
-  if (DFT && doubled) fast_dispatch<E, DFT, true>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
-  else fast_dispatch<E, DFT, false>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj);
+  if (DFT && doubled) fast_dispatch<E, DFT, true>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj, keys);
+  else fast_dispatch<E, DFT, false>(g, cb, h0, lam, xw, s, N, bits, h_out, bv, bj, keys);
   return group_argmax(g, bv, bj, rv, rj);
 }
 

@@ -37,6 +37,17 @@ struct OmpLaunch {
   double* res_out;
 };
 
+struct PursuitLaunch {
+  const void* y;
+  int64_t batch;
+  int K, algo, max_iter, fast;  // algo: 0 subspace pursuit, 1 CoSaMP
+  double rel_tol;
+  void* x_out;
+  int* supp_out;
+  int* iters_out;
+  double* res_out;
+};
+
 // plan construction
 cudaError_t launch_twiddles(const PlanView& P, void* tw64, void* tw32, cudaStream_t st);
 cudaError_t launch_kernel_vector(const PlanView& P, void* c64, void* c32, cudaStream_t st);
@@ -52,5 +63,10 @@ size_t omp_smem_bytes(const PlanView& P, int K, int path);
 int omp_grid(const PlanView& P, int K, int path, int64_t batch, int* err);
 size_t omp_workspace_bytes(const PlanView& P, int K, int grid);
 cudaError_t launch_omp(const PlanView& P, const OmpLaunch& a, void* ws, int grid, cudaStream_t st);
+
+// subspace pursuit / CoSaMP
+int pursuit_grid(const PlanView& P, int K, int algo, int fast, int64_t batch, int* err);
+size_t pursuit_workspace_bytes(const PlanView& P, int K, int algo, int grid);
+cudaError_t launch_pursuit(const PlanView& P, const PursuitLaunch& a, void* ws, int grid, cudaStream_t st);
 
 }  // namespace csf

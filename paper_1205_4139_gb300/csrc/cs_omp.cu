@@ -20,8 +20,8 @@
 // vector c is staged once per CTA in shared memory and shared by both slots;
 // the transform path uses the same region as its buffer, after which c is
 // staged again before the next kernel sum.
-#include "cs_blocks.cuh"
 #include "cs_internal.h"
+#include "cs_ls.cuh"
 
 namespace csf {
 
@@ -206,99 +206,44 @@ __device__ void corr_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const
 
 // -------------------------------------------------- least-squares group
 template <class E>
-__device__ void ls_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const SlotView<E>& v, int& st_out,
-                        double& invd_out, typename FT<E>::W& zeta_out) {
-  using W = typename FT<E>::W;
-  constexpr bool DFT = FT<E>::C;
+__device__ void ls_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const SlotView<E>& v,
+                        LsShared<typename FT<E>::W>& sh) {
   if (S.state != NEED_LS) return;
-  const int N = a.P.N, M = a.P.M, K = a.K;
+  const int K = a.K;
   const int64_t b = S.b;
   const int p = S.p, l = S.lnew;
   const double ynorm2 = S.ynorm2;
-  const double c0 = re(a.P.c64[0]);                      // c(0) = M/N
-  const double dep = 1e-10 * ((double)M / (double)N);    // dependence threshold on d^2
   if (l < 0) {  // no candidate column left
     write_outputs(g, a, v, b, p, ynorm2, S.rn2);
     g.sync();
     if (g.tid == 0) S.state = NEED_INIT;
     return;
   }
-  for (int k = g.tid; k < p; k += g.n) {
-    const int d = DFT ? ((v.lam[k] - l) & (N - 1)) : (v.lam[k] ^ l);
-    v.g[k] = a.P.c64[d];                                  // G(lambda_k, lambda)
-  }
-  g.sync();
-  // g <- u = B g; the finishing threads leave |u_k|^2 and conj(u_k) z_k in
-  // `terms`, placed after the chunk partials of the same buffer
-  double* terms = (double*)(v.part + (2 * kLThreads > K ? 2 * kLThreads : K));
-  tri_matvec(g, v.B, v.g, v.part, p, v.z, terms);
-  // d^2 and u^H z: one warp adds the terms, one thread runs the scalar FP64
-  // work (a warp FP64 instruction costs the same whatever its active lanes,
-  // so the other warps wait at the barrier instead of repeating it).  It is
-  // the group's last warp: the first warps already carry the combines of the
-  // low k.
-  const int lw = g.nwarps() - 1;
-  if (g.warp() == lw) {
-    double an = 0.0, ar = 0.0, ai = 0.0;
-    for (int k = g.lane(); k < p; k += 32) {
-      an += terms[3 * k];
-      ar += terms[3 * k + 1];
-      ai += terms[3 * k + 2];
-    }
-    an = warp_sum(an);
-    ar = warp_sum(ar);
-    if constexpr (DFT) ai = warp_sum(ai);
-    if (g.lane() == 0) {
-      const double d2 = c0 - an;
-      int st = 0;
-      if (!(d2 > dep)) {
-        st = 1;                                          // column dependent on Lambda
-      } else {
-        const double invd = rsqrt(d2);
-        const W bp = to_w(v.h0[l]);                       // (Phi^H y)(lambda)
-        const W zeta = scale(sub(bp, make_w<W>(ar, ai)), invd);
-        const double r2 = S.rn2 - norm2(zeta);
-        S.rn2 = r2;
-        invd_out = invd;
-        zeta_out = zeta;
-        if (p + 1 >= K || r2 < a.rel_tol * a.rel_tol * ynorm2) st = 2;  // step 8
-      }
-      st_out = st;
-    }
-  }
-  g.sync();
-  const int st = st_out;
-  if (st == 1) {
+  LsView<E> lv;
+  lv.B = v.B;
+  lv.z = v.z;
+  lv.x = v.x;
+  lv.g = v.g;
+  lv.part = v.part;
+  lv.terms = (double*)(v.part + (2 * kLThreads > K ? 2 * kLThreads : K));
+  lv.xw = v.xw;
+  lv.lam = v.lam;
+  lv.bits = v.bits;
+  lv.kidx = v.kidx;
+  ls_append(g, a.P, lv, v.h0, p, l, S.rn2, sh);          // step 6
+  if (sh.st == 1) {                                       // column dependent on Lambda
     write_outputs(g, a, v, b, p, ynorm2, S.rn2);
     g.sync();
     if (g.tid == 0) S.state = NEED_INIT;
     return;
   }
-  const double invd = invd_out;
-  const W zeta = zeta_out;
-  tri_vecmat_row(g, v.B, v.g, v.part, p, -invd);         // row p of B (part[0..p))
-  for (int k = g.tid; k < p; k += g.n) {
-    const W xk = fmacv(v.x[k], v.part[k], zeta);
-    v.x[k] = xk;
-    v.xw[k] = from_w<E>(xk);
-  }
-  if (g.tid == 0) {
-    v.B[pidx(p) + p] = make_w<W>(invd, 0.0);
-    v.z[p] = zeta;
-    const W xp = scale(zeta, invd);
-    v.x[p] = xp;
-    v.xw[p] = from_w<E>(xp);
-    v.lam[p] = l;
-    v.kidx[l] = (uint16_t)p;
-    v.bits[l >> 5] |= 1u << (l & 31);
-  }
-  g.sync();
-  if (st == 2) {
+  if (p + 1 >= K || S.rn2 < a.rel_tol * a.rel_tol * ynorm2) {  // step 8
     write_outputs(g, a, v, b, p + 1, ynorm2, S.rn2);
     g.sync();
     if (g.tid == 0) S.state = NEED_INIT;
     return;
   }
+  g.sync();  // every thread has read S.rn2 before it is next written
   if (g.tid == 0) {
     S.p = p + 1;
     S.state = NEED_CORR;
@@ -311,9 +256,8 @@ __global__ void __launch_bounds__(kOmpThreads, (sizeof(E) > 8 ? 1 : 2)) omp_kern
   using V = typename NormT<E>::V;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ SlotState S[2];
-  __shared__ int c_valid, l_state;
-  __shared__ double l_invd;
-  __shared__ W l_zeta;
+  __shared__ int c_valid;
+  __shared__ LsShared<W> l_sh;
   const OmpLayout<E> L = omp_layout<E>(a.P.N, a.K, a.path);
   E* regA = (E*)(sm + L.regA);
   const SlotView<E> v0 = slot_view(sm, L, 0, a), v1 = slot_view(sm, L, 1, a);
@@ -342,7 +286,7 @@ __global__ void __launch_bounds__(kOmpThreads, (sizeof(E) > 8 ? 1 : 2)) omp_kern
       corr_step<E>(gC, a, S[sc], sc ? v1 : v0, regA, (double*)(sm + L.redC), (V*)(sm + L.rvC), (int*)(sm + L.rjC),
                    c_valid);
     } else {
-      ls_step<E>(gL, a, S[sc ^ 1], sc ? v0 : v1, l_state, l_invd, l_zeta);
+      ls_step<E>(gL, a, S[sc ^ 1], sc ? v0 : v1, l_sh);
     }
   }
 }

@@ -32,7 +32,7 @@ def _outputs(B, K, kind):
 
 
 def _call(fn, plan, y, K, outs, path):
-    halt = binding.Halt(1e-6, binding.PATHS[path], -1)
+    halt = binding.Halt(1e-6, binding.PATHS[path], -1, 0)
     p = lambda t: ctypes.c_void_p(t.data_ptr())
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     st = fn(plan._h, p(y), y.shape[0], K, ctypes.byref(halt), p(outs[0]), p(outs[1]), p(outs[2]), p(outs[3]),
@@ -72,12 +72,12 @@ def test_noalloc_rejects_bad_arguments():
     plan = binding.Plan(64, inst["omega"], "dft", "fp32")
     y = torch.from_numpy(inst["Y"]).cuda()
     outs = _outputs(2, 4, "dft")
-    halt = binding.Halt(1e-6, 2, -1)
+    halt = binding.Halt(1e-6, 2, -1, 0)
     p = lambda t: ctypes.c_void_p(t.data_ptr())
     # K larger than M is invalid
     assert L.cs_omp_noalloc(plan._h, p(y), 2, 21, ctypes.byref(halt), p(outs[0]), p(outs[1]), p(outs[2]),
                             p(outs[3]), None) == 1
     # unknown path
-    bad = binding.Halt(1e-6, 7, -1)
+    bad = binding.Halt(1e-6, 7, -1, 0)
     assert L.cs_omp_noalloc(plan._h, p(y), 2, 4, ctypes.byref(bad), p(outs[0]), p(outs[1]), p(outs[2]),
                             p(outs[3]), None) == 1
