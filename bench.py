@@ -143,6 +143,78 @@ def correlation_flops(N: int, iters: np.ndarray, t_switch: int, path: str) -> fl
     return total
 
 
+def _events_ms(fn, steps, warmup, stream, flush=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        out.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in out]
+
+
+def secondary(args, dev, plan, inst, stream, flush):
+    """Measurements beside the headline (not part of the timed step):
+    subspace pursuit on the same batch; single-instance latency on the
+    partial-WHT FP64 case (N=1024, M=256, K=16, noiseless); fast vs
+    transform CoSaMP time per iteration at M=64, N=8192, K=4 (the case the
+    paper quotes for CoSaMP, Sec. IV)."""
+    import torch
+    from paper_1205_4139_gb300 import binding
+    from paper_1205_4139_gb300 import costmodel
+    out = {}
+    B, K = inst["B"], inst["K"]
+    y = torch.from_numpy(inst["Y"]).to(dev)
+    x = torch.empty(B, K, dtype=torch.complex128, device=dev)
+    supp = torch.empty(B, K, dtype=torch.int32, device=dev)
+    it = torch.empty(B, dtype=torch.int32, device=dev)
+    rn = torch.empty(B, dtype=torch.float64, device=dev)
+    ms = _events_ms(lambda: plan.pursuit_into("sp", y, K, x, supp, it, rn, path="fast"), 3, 1, stream, flush)
+    out["sp_fast"] = {"solves_per_s": B / (statistics.median(ms) * 1e-3), "ms_per_step_p50": statistics.median(ms),
+                      "iters_mean": float(it.float().mean())}
+
+    c1 = dict(synth.CONFIG_WHT_FP64_SINGLE)
+    i1 = synth.make_batch(**c1)
+    p1 = binding.Plan(c1["N"], i1["omega"], "wht", "fp64")
+    y1 = torch.from_numpy(i1["Y"]).to(dev)
+    x1 = torch.empty(1, c1["K"], dtype=torch.float64, device=dev)
+    s1 = torch.empty(1, c1["K"], dtype=torch.int32, device=dev)
+    t1 = torch.empty(1, dtype=torch.int32, device=dev)
+    r1 = torch.empty(1, dtype=torch.float64, device=dev)
+    lat = {}
+    for path in ("fast", "conv", "hybrid"):
+        v = sorted(_events_ms(lambda: p1.omp_into(y1, c1["K"], x1, s1, t1, r1, path=path), 200, 10, stream))
+        lat[path] = {"p50_us": 1e3 * statistics.median(v), "p99_us": 1e3 * v[int(0.99 * (len(v) - 1))]}
+    out["omp_wht_fp64_single_latency"] = {"config": "partial WHT FP64, N=1024, M=256, K=16, noiseless, 1 instance",
+                                          **lat}
+
+    rng_inst = synth.make_batch("dft", 8192, 64, 4, 256, snr_db=None, prec="fp32", seed=3)
+    p3 = binding.Plan(8192, rng_inst["omega"], "dft", "fp32")
+    y3 = torch.from_numpy(rng_inst["Y"]).to(dev)
+    B3 = y3.shape[0]
+    x3 = torch.empty(B3, 4, dtype=torch.complex128, device=dev)
+    s3 = torch.empty(B3, 4, dtype=torch.int32, device=dev)
+    t3 = torch.empty(B3, dtype=torch.int32, device=dev)
+    r3 = torch.empty(B3, dtype=torch.float64, device=dev)
+    per_it = {}
+    for path in ("fast", "conv"):
+        v = _events_ms(lambda: p3.pursuit_into("cosamp", y3, 4, x3, s3, t3, r3, path=path, max_iter=8), 20, 3,
+                       stream, flush)
+        per_it[path] = statistics.median(v) / max(1.0, float(t3.sum()))
+    out["cosamp_M64_N8192_K4"] = {"ms_per_instance_iteration": per_it,
+                                  "fast_over_conv": per_it["fast"] / per_it["conv"],
+                                  "paper_flop_model": costmodel.cosamp_fast_ratio(8192, 4)}
+    return out
+
+
 def run_gpu(args, rank: int, world: int):
     import torch
     from paper_1205_4139_gb300 import binding
@@ -227,6 +299,8 @@ def run_gpu(args, rank: int, world: int):
     h2d = y.numel() * y.element_size()
     d2h = sum(t.numel() * t.element_size() for t in (x, supp, iters, rn))
 
+    extra = secondary(args, dev, plan, inst, stream, flush) if (rank == 0 and not args.no_extra) else {}
+
     # max over ranks
     vals = torch.tensor([total_ms, sum(e2e_ms) / len(e2e_ms), statistics.median(fast_ms),
                          statistics.median(conv_ms)], dtype=torch.float64, device=dev)
@@ -254,6 +328,7 @@ def run_gpu(args, rank: int, world: int):
         "clocks": clk.summary(),
         "gpu_launches": args.steps,
         "iters_mean": float(it_np.mean()),
+        "extra": extra,
     }
 
 
@@ -263,7 +338,8 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle instances (default 2 per core)")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle instances (default one per core)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", 0))
@@ -322,7 +398,7 @@ def main():
                 "fast": r["fast"], "conv": r["conv"], "plan_ms": r["plan_ms"],
                 "t_switch_default": r["t_switch_default"], "t_switch_sweep_ms": r["t_switch_sweep_ms"],
                 "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
-                "gpu_launches": r["gpu_launches"]}
+                "gpu_launches": r["gpu_launches"], "secondary": r["extra"]}
         print(json.dumps(line))
     if world > 1:
         import torch
