@@ -69,7 +69,9 @@ typedef enum { CS_PATH_FAST = 0, CS_PATH_CONV = 1, CS_PATH_HYBRID = 2 } cs_path;
  * the tolerance).  A zero measurement halts before the first iteration; a
  * selected column whose Cholesky pivot is <= 1e-10 * M/N (numerically
  * dependent on the support) ends the run without being added.
- * t_switch < 0 selects the plan's default switch point (cs_plan_info).
+ * t_switch < 0 selects the plan's switch point: the one cs_plan_tune
+ * measured, if it has run on this plan, else the flop-model default
+ * (cs_plan_info).
  * max_iter bounds the iterations of cs_sp / cs_cosamp (<= 0: K for SP, 50 for
  * CoSaMP); cs_omp ignores it (its bound is K). */
 typedef struct {
@@ -91,10 +93,10 @@ cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_
 /* Release the plan's device memory (synchronises the device first). */
 cs_status cs_plan_destroy(cs_plan_t plan);
 
-/* Report the plan's sizes and its default hybrid switch point: the largest t
- * whose kernel-sum cost is no more than one transform's in the flop model of
- * Table I (Sec. IV's "excessive point"), unless the library was tuned for
- * this (kind, prec, N). Any output pointer may be NULL. */
+/* Report the plan's sizes and its flop-model hybrid switch point: the
+ * largest t whose kernel-sum cost is no more than one transform's in the flop
+ * model of Table I (Sec. IV's "excessive point").  Any output pointer may be
+ * NULL. */
 cs_status cs_plan_info(cs_plan_t plan, int64_t* N, int64_t* M, int32_t* kind, int32_t* prec,
                        int32_t* t_switch_default);
 
@@ -187,6 +189,22 @@ cs_status cs_cosamp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K,
 cs_status cs_omp_noalloc(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K,
                          const cs_halt* halt, void* x_dev, int32_t* supp_dev, int32_t* iters_dev,
                          double* resnorm_dev, void* stream);
+
+/* Measure the hybrid switch point (Sec. IV's adaptive strategy, with the
+ * crossover measured instead of taken from the flop model of Table I).
+ * Runs cs_omp with CS_PATH_HYBRID on the caller's batch (y_dev, batch, K,
+ * rel_tol) at a ladder of switch points: 1 (transforms from t = 2 on), the
+ * flop-model point, 8, 12, 16, 24, 36, ... and K (kernel sums throughout);
+ * each is timed with CUDA events on `stream` (one warm-up, best of three).
+ * The fastest becomes the plan's switch point for calls that pass
+ * t_switch < 0, and is written to *t_best.  If cap > 0, the first
+ * min(cap, n) ladder entries and their times in ms go to cand_out (int32) and
+ * ms_out (float), and n to *n_out (NULL allowed).  Allocates its temporary
+ * outputs on `stream`, overwrites the plan's workspace and blocks until done.
+ * Limits: those of cs_omp with 1 <= K, batch >= 1. */
+cs_status cs_plan_tune(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, double rel_tol,
+                       int32_t* t_best, int32_t* cand_out, float* ms_out, int32_t cap, int32_t* n_out,
+                       void* stream);
 
 /* Short static description of a status code. */
 const char* cs_status_string(cs_status s);

@@ -23,8 +23,8 @@ PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 
 # Every function include/csfast.h declares.
 EXPORTS = ["cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
-           "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_status_string",
-           "cs_last_error"]
+           "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
+           "cs_status_string", "cs_last_error"]
 
 
 class CsError(RuntimeError):
@@ -61,8 +61,10 @@ def load(path: str = LIB_PATH):
     L.cs_omp_noalloc.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_sp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_cosamp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
+    L.cs_plan_tune.argtypes = [vp, vp, i64, i32, ctypes.c_double, pi32, pi32, ctypes.POINTER(ctypes.c_float), i32,
+                               pi32, vp]
     for f in ("cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
-              "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc"):
+              "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune"):
         getattr(L, f).restype = ctypes.c_int
     L.cs_status_string.argtypes = [ctypes.c_int]
     L.cs_status_string.restype = ctypes.c_char_p
@@ -130,6 +132,18 @@ class Plan:
         _check(load().cs_plan_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(k), ctypes.byref(p),
                                    ctypes.byref(ts)))
         return {"N": n.value, "M": m.value, "kind": k.value, "prec": p.value, "t_switch_default": ts.value}
+
+    def tune(self, y, K: int, rel_tol: float = 1e-6, stream=None) -> tuple[int, dict]:
+        """cs_plan_tune: measure the hybrid switch point on (batch, M) y; returns
+        (t_best, {t_switch: ms})."""
+        self._want(y, self.M)
+        cap = 64
+        cand = (ctypes.c_int32 * cap)()
+        ms = (ctypes.c_float * cap)()
+        tb, n = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().cs_plan_tune(self._h, _ptr(y), y.shape[0], K, rel_tol, ctypes.byref(tb), cand, ms, cap,
+                                   ctypes.byref(n), _stream(stream)))
+        return tb.value, {int(cand[i]): float(ms[i]) for i in range(min(cap, n.value))}
 
     def device_error(self, stream=None) -> int:
         """Kernel-detected error bits since the last call (cs_plan_status)."""

@@ -17,6 +17,7 @@ struct cs_plan_s {
   int kind, prec;
   int device;
   int t_switch_default;
+  int t_switch_tuned = -1;  // set by cs_plan_tune
   int* d_slot = nullptr;
   void* d_tw64 = nullptr;
   void* d_tw32 = nullptr;
@@ -61,6 +62,10 @@ const PlanView* plan_view(cs_plan_t plan) { return &plan->v; }
 int plan_t_switch_default(cs_plan_t plan) { return plan->t_switch_default; }
 void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 }  // namespace csf
+
+// Switch point used when a call passes t_switch < 0: the measured one once
+// cs_plan_tune has run, else the flop-model default.
+static int plan_switch(const cs_plan_s* p) { return p->t_switch_tuned >= 0 ? p->t_switch_tuned : p->t_switch_default; }
 
 static void plan_free(cs_plan_s* p) {
   if (!p) return;
@@ -234,7 +239,7 @@ extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, in
   if (batch == 0) return CS_OK;
   if (K > 0 && !supp_dev) return CS_ERR_INVALID;
   if (plan->v.M > 0 && !y_dev) return CS_ERR_INVALID;
-  const int t_switch = h.t_switch < 0 ? plan->t_switch_default : h.t_switch;
+  const int t_switch = h.t_switch >= 0 ? h.t_switch : plan_switch(plan);
   cudaStream_t st = (cudaStream_t)stream;
 
   int err = 0;
@@ -275,7 +280,7 @@ static cs_status pursuit_call(int algo, cs_plan_t plan, const void* y_dev, int64
   if (h.path != CS_PATH_FAST && h.path != CS_PATH_CONV && h.path != CS_PATH_HYBRID) return CS_ERR_INVALID;
   if (batch == 0) return CS_OK;
   if (!supp_dev || !y_dev) return CS_ERR_INVALID;
-  const int t_switch = h.t_switch < 0 ? plan->t_switch_default : h.t_switch;
+  const int t_switch = h.t_switch >= 0 ? h.t_switch : plan_switch(plan);
   const int fast = h.path == CS_PATH_FAST || (h.path == CS_PATH_HYBRID && K <= t_switch);
   cudaStream_t st = (cudaStream_t)stream;
   int err = 0;
@@ -314,4 +319,85 @@ extern "C" cs_status cs_cosamp(cs_plan_t plan, const void* y_dev, int64_t batch,
                                void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev,
                                void* stream) {
   return pursuit_call(1, plan, y_dev, batch, K, halt, x_dev, supp_dev, iters_dev, resnorm_dev, stream);
+}
+
+// Switch-point tuning (Sec. IV: the paper picks the switch from its flop
+// model; here the crossover is measured).  Runs cs_omp on the caller's batch
+// with the hybrid path at a ladder of switch points and keeps the fastest.
+extern "C" cs_status cs_plan_tune(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, double rel_tol,
+                                  int32_t* t_best, int32_t* cand_out, float* ms_out, int32_t cap, int32_t* n_out,
+                                  void* stream) {
+  if (!plan || !t_best || batch < 1 || K < 1 || K > plan->v.M || cap < 0) return CS_ERR_INVALID;
+  if ((cap > 0 && (!cand_out || !ms_out)) || !(rel_tol >= 0.0) || !std::isfinite(rel_tol)) return CS_ERR_INVALID;
+  if (plan->v.M > 0 && !y_dev) return CS_ERR_INVALID;
+  if (K > kMaxK) return CS_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  // ladder: 1 (transforms from t = 2 on), the flop-model point, then roughly
+  // geometric steps up to K (kernel sums throughout)
+  std::vector<int> cand = {1, plan->t_switch_default};
+  for (int t = 8; t < K; t = t < 16 ? t + 4 : t + t / 2) cand.push_back(t);
+  cand.push_back(K);
+  std::vector<int> ladder;
+  for (int t : cand) {
+    const int u = t < 1 ? 1 : (t > K ? K : t);
+    bool seen = false;
+    for (int v : ladder) seen = seen || v == u;
+    if (!seen) ladder.push_back(u);
+  }
+  for (size_t i = 1; i < ladder.size(); ++i)
+    for (size_t j = i; j > 0 && ladder[j - 1] > ladder[j]; --j) std::swap(ladder[j - 1], ladder[j]);
+
+  const size_t wb = elem_bytes(plan->kind, CS_FP64);
+  void* x = nullptr;
+  int32_t* supp = nullptr;
+  cs_status rc = CS_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<float> ms(ladder.size(), 0.0f);
+  do {
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&x, (size_t)batch * K * wb, st)) != cudaSuccess) { rc = cuda_fail(e, "tune alloc"); break; }
+    if ((e = cudaMallocAsync((void**)&supp, (size_t)batch * K * sizeof(int32_t), st)) != cudaSuccess) {
+      rc = cuda_fail(e, "tune alloc");
+      break;
+    }
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+      rc = cuda_fail(e, "tune events");
+      break;
+    }
+    for (size_t i = 0; i < ladder.size() && rc == CS_OK; ++i) {
+      const cs_halt h = {rel_tol, CS_PATH_HYBRID, ladder[i], 0};
+      float best = 0.0f;
+      for (int rep = 0; rep < 4 && rc == CS_OK; ++rep) {  // one warm-up, best of three
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { rc = cuda_fail(e, "tune record"); break; }
+        rc = cs_omp(plan, y_dev, batch, K, &h, x, supp, nullptr, nullptr, stream);
+        if (rc != CS_OK) break;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+          rc = cuda_fail(e, "tune timing");
+          break;
+        }
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep == 1 || (rep > 1 && t < best)) best = t;
+      }
+      ms[i] = best;
+    }
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (x) cudaFreeAsync(x, st);
+  if (supp) cudaFreeAsync(supp, st);
+  if (rc != CS_OK) return rc;
+  CS_CUDA(cudaStreamSynchronize(st), "tune synchronize");
+  size_t bi = 0;
+  for (size_t i = 1; i < ladder.size(); ++i)
+    if (ms[i] < ms[bi]) bi = i;
+  plan->t_switch_tuned = ladder[bi];
+  *t_best = ladder[bi];
+  const int n = (int)ladder.size() < cap ? (int)ladder.size() : cap;
+  for (int i = 0; i < n; ++i) {
+    cand_out[i] = ladder[i];
+    ms_out[i] = ms[i];
+  }
+  if (n_out) *n_out = (int)ladder.size();
+  return CS_OK;
 }
