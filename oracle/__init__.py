@@ -11,6 +11,8 @@ Contents (each function cites the passage of the paper it follows):
 * ``omp``        Algorithm 1.1 (conventional OMP) with dense Phi^H r
 * ``kernelsum``  the correlation kernel vector c, the permutations P_lambda of
                  Theorem 2-1 and the fast correlation of Eq. (kernelsum)
+* ``transform``  Algorithm 1.1 for large N with Phi applied through FFT / FWHT
+                 (pinned against ``omp`` at N <= 4096)
 * ``pursuits``   subspace pursuit and CoSaMP in their standard forms (parity
                  unpinned beyond recovery, OMP agreement on 1-sparse signals
                  and least-squares optimality: the paper defines neither)
@@ -18,4 +20,4 @@ Contents (each function cites the passage of the paper it follows):
 Everything is plain numpy in float64 / complex128 with no blocking, fusion or
 reordering beyond what the definitions state.
 """
-from . import matrices, omp, kernelsum, pursuits  # noqa: F401
+from . import matrices, omp, kernelsum, pursuits, transform  # noqa: F401

@@ -77,3 +77,39 @@ def test_dropped_kernel_term_is_caught(monkeypatch):
     bad_fast_impl = lambda kind, N, c, h0, support, x: orig(kind, N, c, h0, support[:-1], x[:-1])
     monkeypatch.setattr(kernelsum, "fast_correlation_dense", bad_fast_impl)
     caught(pins.test_fast_equals_conventional, "wht")
+
+
+# --------------------------------------------- large-N (transform) oracle
+def test_transform_forward_for_adjoint_is_caught(monkeypatch):
+    import tests.test_oracle_transform as tpins
+    from oracle import transform
+    monkeypatch.setattr(transform, "apply_AH",
+                        lambda kind, v: transform.apply_A(kind, v) if kind == "dft" else transform.fwht(v) / np.sqrt(v.shape[-1]))
+    caught(tpins.test_correlate_and_synthesize_match_dense, "dft", 64, 20)
+
+
+def test_transform_butterfly_slip_is_caught(monkeypatch):
+    import tests.test_oracle_transform as tpins
+    from oracle import transform
+
+    def bad_fwht(v):
+        a = np.array(v, dtype=float, copy=True)
+        N = a.shape[-1]
+        lead = a.shape[:-1]
+        h = 1
+        while h < N:
+            a = a.reshape(*lead, N // (2 * h), 2, h)
+            top, bot = a[..., 0, :], a[..., 1, :]
+            a = np.stack((top + bot, bot - top), axis=-2)   # sign of the difference flipped
+            h *= 2
+        return a.reshape(*lead, N)
+    monkeypatch.setattr(transform, "fwht", bad_fwht)
+    caught(tpins.test_fwht_is_sylvester, 16)
+
+
+def test_transform_residual_sign_is_caught(monkeypatch):
+    import tests.test_oracle_transform as tpins
+    from oracle import transform
+    orig = transform.synthesize
+    monkeypatch.setattr(transform, "synthesize", lambda *a: -orig(*a))
+    caught(tpins.test_omp_matches_dense_oracle, "wht", 1024, 256, 16, None)
