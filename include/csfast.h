@@ -85,8 +85,12 @@ typedef struct {
  * correlation kernel vector c = U^H S^T S U e_1 of Eq. (kernelsum) in FP64
  * (and rounded to FP32 for FP32 plans), the transform twiddles and the index
  * maps of Omega.  `omega_host` is a host array of M int32 (M may be 0).
- * Blocks until the plan's tables are built.  Limits: 1 <= N <= 8192 (whole
- * instance on one SM), 0 <= M <= N. */
+ * Blocks until the plan's tables are built.  Limits: 1 <= N <= 2^24,
+ * 0 <= M <= N.  Plans with N <= 8192 keep a whole instance on one SM (one
+ * fused kernel per call); larger plans spread each instance over the GPU
+ * with four-step transforms through global memory and queue a short
+ * sequence of kernels per OMP iteration (at most 65535 instances per call;
+ * cs_sp, cs_cosamp and cs_omp_noalloc return CS_ERR_UNSUPPORTED for them). */
 cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind,
                          int32_t prec, void* stream, cs_plan_t* out);
 

@@ -23,6 +23,8 @@ struct cs_plan_s {
   void* d_tw32 = nullptr;
   void* d_c64 = nullptr;
   void* d_c32 = nullptr;
+  void* d_lt64 = nullptr;   // large plans: four-step tables (FP64)
+  void* d_lt32 = nullptr;   // large plans: four-step tables (FP32)
   int* d_status = nullptr;  // kernel-detected errors (cs_plan_status)
   void* ws = nullptr;       // OMP workspace (grows on demand, stream-ordered)
   size_t ws_bytes = 0;
@@ -74,9 +76,22 @@ static void plan_free(cs_plan_s* p) {
   cudaFree(p->d_tw32);
   cudaFree(p->d_c64);
   cudaFree(p->d_c32);
+  cudaFree(p->d_lt64);
+  cudaFree(p->d_lt32);
   cudaFree(p->d_status);
   cudaFree(p->ws);
   delete p;
+}
+
+// Grows the plan's workspace to `need` bytes (stream-ordered).
+static cs_status ensure_ws(cs_plan_s* plan, size_t need, cudaStream_t st) {
+  if (need <= plan->ws_bytes) return CS_OK;
+  if (plan->ws) CS_CUDA(cudaFreeAsync(plan->ws, st), "cudaFreeAsync workspace");
+  plan->ws = nullptr;
+  plan->ws_bytes = 0;
+  CS_CUDA(cudaMallocAsync(&plan->ws, need, st), "cudaMallocAsync workspace");
+  plan->ws_bytes = need;
+  return CS_OK;
 }
 
 extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
@@ -94,7 +109,8 @@ extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_
   }
   int logN = 0;
   while ((int64_t(1) << logN) < N) ++logN;
-  if (logN > kMaxLogN) return CS_ERR_UNSUPPORTED;
+  if (logN > kMaxLogNLarge) return CS_ERR_UNSUPPORTED;
+  const bool large = logN > kMaxLogN;
 
   cs_plan_s* p = new (std::nothrow) cs_plan_s();
   if (!p) return CS_ERR_NOMEM;
@@ -107,14 +123,19 @@ extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_
   p->v.M = (int)M;
   p->v.dft = kind == CS_DFT;
   p->v.fp32 = prec == CS_FP32;
+  p->v.large = large;
+  p->v.n1 = large ? logN / 2 : 0;
+  p->v.n2 = large ? logN - logN / 2 : 0;
+  p->v.wsh = large ? (logN + 1) / 2 : 0;
   // Sec. IV excessive point under the Table I flop model
   p->t_switch_default = kind == CS_DFT ? 1 + (5 * logN) / 6 : 1 + logN;
 
-  // slot map: position -> m.  DFT positions are those of the forward DIF
-  // chain (the adjoint chain's input order); WHT positions are natural.
+  // slot map: position -> m.  DFT positions of one-CTA plans are those of
+  // the forward DIF chain (the adjoint chain's input order); WHT positions
+  // and those of large plans are natural.
   std::vector<int32_t> slot((size_t)N, -1);
   for (int64_t m = 0; m < M; ++m) {
-    const int pos = kind == CS_DFT ? dif_position(omega_host[m], logN) : omega_host[m];
+    const int pos = (kind == CS_DFT && !large) ? dif_position(omega_host[m], logN) : omega_host[m];
     slot[(size_t)pos] = (int32_t)m;
   }
   const size_t wb = kind == CS_DFT ? 16 : 8;
@@ -131,9 +152,15 @@ extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_
   PLAN_TRY(cudaMalloc(&p->d_slot, (size_t)N * sizeof(int32_t)), "cudaMalloc slot");
   PLAN_TRY(cudaMemcpyAsync(p->d_slot, slot.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, st),
            "copy slot");
-  if (kind == CS_DFT) {
+  if (kind == CS_DFT && !large) {
     PLAN_TRY(cudaMalloc(&p->d_tw64, (size_t)N * sizeof(double2)), "cudaMalloc twiddles");
     if (prec == CS_FP32) PLAN_TRY(cudaMalloc(&p->d_tw32, (size_t)N * sizeof(float2)), "cudaMalloc twiddles");
+  }
+  if (kind == CS_DFT && large) {
+    const size_t nt = ((size_t)1 << p->v.n1) + ((size_t)1 << p->v.n2) + ((size_t)1 << p->v.wsh) +
+                      ((size_t)N >> p->v.wsh);
+    PLAN_TRY(cudaMalloc(&p->d_lt64, nt * sizeof(double2)), "cudaMalloc four-step tables");
+    if (prec == CS_FP32) PLAN_TRY(cudaMalloc(&p->d_lt32, nt * sizeof(float2)), "cudaMalloc four-step tables");
   }
   PLAN_TRY(cudaMalloc(&p->d_c64, (size_t)N * wb), "cudaMalloc c");
   if (prec == CS_FP32) PLAN_TRY(cudaMalloc(&p->d_c32, (size_t)N * wb / 2), "cudaMalloc c");
@@ -145,9 +172,22 @@ extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_
   p->v.c64 = p->d_c64;
   p->v.c32 = p->d_c32;
   p->v.status = p->d_status;
-  if (kind == CS_DFT) PLAN_TRY(launch_twiddles(p->v, p->d_tw64, p->d_tw32, st), "twiddle kernel");
-  PLAN_TRY(launch_kernel_vector(p->v, p->d_c64, p->d_c32, st), "kernel-vector kernel");
-  PLAN_TRY(cudaStreamSynchronize(st), "plan synchronize");
+  p->v.lt64 = p->d_lt64;
+  p->v.lt32 = p->d_lt32;
+  if (!large) {
+    if (kind == CS_DFT) PLAN_TRY(launch_twiddles(p->v, p->d_tw64, p->d_tw32, st), "twiddle kernel");
+    PLAN_TRY(launch_kernel_vector(p->v, p->d_c64, p->d_c32, st), "kernel-vector kernel");
+    PLAN_TRY(cudaStreamSynchronize(st), "plan synchronize");
+  } else {
+    void* tmp = nullptr;
+    PLAN_TRY(large_tables(p->v, p->d_lt64, p->d_lt32, st), "four-step tables");
+    PLAN_TRY(cudaMalloc(&tmp, (size_t)N * wb), "cudaMalloc plan scratch");
+    e = large_kernel_vector(p->v, p->d_c64, p->d_c32, tmp, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    PLAN_TRY(e, "kernel-vector kernels");
+    PLAN_TRY(e2, "plan synchronize");
+  }
 #undef PLAN_TRY
   *out = p;
   return CS_OK;
@@ -198,10 +238,8 @@ extern "C" cs_status cs_plan_kernel(cs_plan_t plan, void* c_dev, int32_t prec, v
             "copy c");
     return CS_OK;
   }
-  // FP64 plan asked for FP32 c: round through a temporary plan view
-  PlanView v = plan->v;
-  v.fp32 = true;
-  CS_CUDA(launch_kernel_vector(v, plan->d_c64, c_dev, (cudaStream_t)stream), "round c");
+  // FP64 plan asked for FP32 c: round the FP64 vector
+  CS_CUDA(launch_round(plan->v.dft, plan->d_c64, c_dev, plan->v.N, (cudaStream_t)stream), "round c");
   return CS_OK;
 }
 
@@ -210,6 +248,14 @@ extern "C" cs_status cs_correlate(cs_plan_t plan, const void* r_dev, int64_t bat
   if (!plan || batch < 0) return CS_ERR_INVALID;
   if (batch > 0 && plan->v.M > 0 && !r_dev) return CS_ERR_INVALID;
   if (batch == 0 || (!h_dev && !argmax_dev)) return CS_OK;
+  if (plan->v.large) {
+    if (batch > kMaxLargeBatch) return CS_ERR_UNSUPPORTED;
+    const cs_status r = ensure_ws(plan, large_correlate_ws(plan->v, batch), (cudaStream_t)stream);
+    if (r != CS_OK) return r;
+    CS_CUDA(large_correlate(plan->v, r_dev, batch, h_dev, argmax_dev, plan->ws, (cudaStream_t)stream),
+            "correlate");
+    return CS_OK;
+  }
   CS_CUDA(launch_correlate(plan->v, r_dev, batch, h_dev, argmax_dev, (cudaStream_t)stream), "correlate");
   return CS_OK;
 }
@@ -222,6 +268,15 @@ extern "C" cs_status cs_correlate_fast(cs_plan_t plan, const void* h0_dev, const
   if (batch > 0 && s > 0 && (!supp_dev || !x_dev)) return CS_ERR_INVALID;
   if (s > kMaxK) return CS_ERR_UNSUPPORTED;
   if (batch == 0 || (!h_dev && !argmax_dev)) return CS_OK;
+  if (plan->v.large) {
+    if (batch > kMaxLargeBatch) return CS_ERR_UNSUPPORTED;
+    const cs_status r = ensure_ws(plan, large_fast_ws(plan->v, batch), (cudaStream_t)stream);
+    if (r != CS_OK) return r;
+    CS_CUDA(large_correlate_fast(plan->v, h0_dev, supp_dev, x_dev, s, batch, h_dev, argmax_dev, plan->ws,
+                                 (cudaStream_t)stream),
+            "correlate_fast");
+    return CS_OK;
+  }
   CS_CUDA(launch_correlate_fast(plan->v, h0_dev, supp_dev, x_dev, s, batch, h_dev, argmax_dev, (cudaStream_t)stream),
           "correlate_fast");
   return CS_OK;
@@ -242,16 +297,16 @@ extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, in
   const int t_switch = h.t_switch >= 0 ? h.t_switch : plan_switch(plan);
   cudaStream_t st = (cudaStream_t)stream;
 
-  int err = 0;
-  const int grid = omp_grid(plan->v, K, h.path, batch, &err);
-  if (err) return cuda_fail((cudaError_t)err, "omp configuration");
-  const size_t need = omp_workspace_bytes(plan->v, K, grid);
-  if (need > plan->ws_bytes) {
-    if (plan->ws) CS_CUDA(cudaFreeAsync(plan->ws, st), "cudaFreeAsync workspace");
-    plan->ws = nullptr;
-    plan->ws_bytes = 0;
-    CS_CUDA(cudaMallocAsync(&plan->ws, need, st), "cudaMallocAsync workspace");
-    plan->ws_bytes = need;
+  int err = 0, grid = 0;
+  if (plan->v.large) {
+    if (batch > kMaxLargeBatch) return CS_ERR_UNSUPPORTED;
+    const cs_status r = ensure_ws(plan, large_omp_ws(plan->v, K, h.path, batch), st);
+    if (r != CS_OK) return r;
+  } else {
+    grid = omp_grid(plan->v, K, h.path, batch, &err);
+    if (err) return cuda_fail((cudaError_t)err, "omp configuration");
+    const cs_status r = ensure_ws(plan, omp_workspace_bytes(plan->v, K, grid), st);
+    if (r != CS_OK) return r;
   }
   OmpLaunch a;
   a.y = y_dev;
@@ -264,7 +319,8 @@ extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, in
   a.supp_out = supp_dev;
   a.iters_out = iters_dev;
   a.res_out = resnorm_dev;
-  CS_CUDA(launch_omp(plan->v, a, plan->ws, grid, st), "omp kernel");
+  if (plan->v.large) CS_CUDA(large_omp(plan->v, a, plan->ws, st), "omp kernels");
+  else CS_CUDA(launch_omp(plan->v, a, plan->ws, grid, st), "omp kernel");
   return CS_OK;
 }
 
@@ -273,7 +329,7 @@ static cs_status pursuit_call(int algo, cs_plan_t plan, const void* y_dev, int64
                               double* resnorm_dev, void* stream) {
   if (!plan || batch < 0 || K < 1) return CS_ERR_INVALID;
   if ((algo == 0 ? 2 : 3) * (int64_t)K > plan->v.M) return CS_ERR_INVALID;
-  if (K > 128) return CS_ERR_UNSUPPORTED;
+  if (K > 128 || plan->v.large) return CS_ERR_UNSUPPORTED;
   cs_halt h = {1e-6, CS_PATH_HYBRID, -1, 0};
   if (halt) h = *halt;
   if (!(h.rel_tol >= 0.0) || !std::isfinite(h.rel_tol)) return CS_ERR_INVALID;
@@ -286,14 +342,8 @@ static cs_status pursuit_call(int algo, cs_plan_t plan, const void* y_dev, int64
   int err = 0;
   const int grid = pursuit_grid(plan->v, K, algo, fast, batch, &err);
   if (err) return cuda_fail((cudaError_t)err, "pursuit configuration");
-  const size_t need = pursuit_workspace_bytes(plan->v, K, algo, grid);
-  if (need > plan->ws_bytes) {
-    if (plan->ws) CS_CUDA(cudaFreeAsync(plan->ws, st), "cudaFreeAsync workspace");
-    plan->ws = nullptr;
-    plan->ws_bytes = 0;
-    CS_CUDA(cudaMallocAsync(&plan->ws, need, st), "cudaMallocAsync workspace");
-    plan->ws_bytes = need;
-  }
+  const cs_status r = ensure_ws(plan, pursuit_workspace_bytes(plan->v, K, algo, grid), st);
+  if (r != CS_OK) return r;
   PursuitLaunch a;
   a.y = y_dev;
   a.batch = batch;

@@ -217,7 +217,8 @@ __device__ __forceinline__ void wht_reg(E (&v)[R]) {
 // ------------------------------------------------------------ thread groups
 // A group of whole warps of one CTA working on one task: `tid` is the thread
 // index within the group, `n` its size, `bar` the hardware barrier it
-// synchronises on (0 = the CTA-wide barrier when the group is the whole CTA).
+// synchronises on (0 = the CTA-wide barrier when the group is the whole CTA,
+// -1 = a group of exactly one warp, which synchronises with __syncwarp).
 // The compiler does not know that the inline named barrier is a barrier, so
 // it would not reconverge a warp whose lanes took different paths before it:
 // __syncwarp() reconverges the warp first, and the non-aligned form counts
@@ -227,6 +228,8 @@ struct Grp {
   __device__ __forceinline__ void sync() const {
     if (bar == 0) {
       __syncthreads();
+    } else if (bar < 0) {  // a group of one warp
+      __syncwarp();
     } else {
       __syncwarp();
       asm volatile("barrier.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");

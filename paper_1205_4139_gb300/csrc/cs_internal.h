@@ -7,8 +7,10 @@
 namespace csf {
 
 constexpr int kThreads = 256;
-constexpr int kMaxLogN = 13;   // N <= 8192: one instance per CTA
+constexpr int kMaxLogN = 13;       // N <= 8192: one instance per CTA
+constexpr int kMaxLogNLarge = 24;  // four-step transforms through global memory
 constexpr int kMaxK = 1024;
+constexpr int kMaxLargeBatch = 65535;  // large plans: instances per call
 
 // Type-erased view of a plan's device tables.
 struct PlanView {
@@ -20,6 +22,14 @@ struct PlanView {
   const void* c64;    // double / double2 [N]
   const void* c32;    // float / float2 [N] (FP32)
   int* status;        // device status word (kernel-detected errors), owned by the plan
+  // large plans (logN > kMaxLogN): N = N1 N2 with N1 = 2^n1, N2 = 2^n2; the
+  // slot map is in natural order and lt64 / lt32 hold, one after the other,
+  // the DIF twiddles of the N1 chain, of the N2 chain, then w_N^m for
+  // m < 2^wsh and w_N^(m 2^wsh) for m < N / 2^wsh (DFT only)
+  bool large;
+  int n1, n2, wsh;
+  const void* lt64;
+  const void* lt32;
 };
 
 // Bits of the device status word.
@@ -50,6 +60,8 @@ struct PursuitLaunch {
 
 // plan construction
 cudaError_t launch_twiddles(const PlanView& P, void* tw64, void* tw32, cudaStream_t st);
+cudaError_t launch_twiddles_log(int logN, void* tw64, void* tw32, cudaStream_t st);
+cudaError_t launch_round(bool dft, const void* c64, void* c32, int n, cudaStream_t st);
 cudaError_t launch_kernel_vector(const PlanView& P, void* c64, void* c32, cudaStream_t st);
 
 // transforms / correlations
@@ -63,6 +75,18 @@ size_t omp_smem_bytes(const PlanView& P, int K, int path);
 int omp_grid(const PlanView& P, int K, int path, int64_t batch, int* err);
 size_t omp_workspace_bytes(const PlanView& P, int K, int grid);
 cudaError_t launch_omp(const PlanView& P, const OmpLaunch& a, void* ws, int grid, cudaStream_t st);
+
+// large plans (cs_large.cu)
+cudaError_t large_tables(const PlanView& P, void* lt64, void* lt32, cudaStream_t st);
+cudaError_t large_kernel_vector(const PlanView& P, void* c64, void* c32, void* tmp, cudaStream_t st);
+size_t large_correlate_ws(const PlanView& P, int64_t batch);
+cudaError_t large_correlate(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax, void* ws,
+                            cudaStream_t st);
+size_t large_fast_ws(const PlanView& P, int64_t batch);
+cudaError_t large_correlate_fast(const PlanView& P, const void* h0, const int32_t* supp, const void* x, int s,
+                                 int64_t batch, void* h, int32_t* amax, void* ws, cudaStream_t st);
+size_t large_omp_ws(const PlanView& P, int K, int path, int64_t batch);
+cudaError_t large_omp(const PlanView& P, const OmpLaunch& a, void* ws, cudaStream_t st);
 
 // subspace pursuit / CoSaMP
 int pursuit_grid(const PlanView& P, int K, int algo, int fast, int64_t batch, int* err);

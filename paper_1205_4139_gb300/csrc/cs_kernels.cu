@@ -53,7 +53,17 @@ __global__ void round_kernel(const W* a, E* b, int n) {
 }
 
 cudaError_t launch_twiddles(const PlanView& P, void* tw64, void* tw32, cudaStream_t st) {
-  twiddle_kernel<<<64, kThreads, 0, st>>>(P.logN, (double2*)tw64, (float2*)tw32);
+  return launch_twiddles_log(P.logN, tw64, tw32, st);
+}
+
+cudaError_t launch_twiddles_log(int logN, void* tw64, void* tw32, cudaStream_t st) {
+  twiddle_kernel<<<64, kThreads, 0, st>>>(logN, (double2*)tw64, (float2*)tw32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round(bool dft, const void* c64, void* c32, int n, cudaStream_t st) {
+  if (dft) round_kernel<double2, float2><<<16, kThreads, 0, st>>>((const double2*)c64, (float2*)c32, n);
+  else round_kernel<double, float><<<16, kThreads, 0, st>>>((const double*)c64, (float*)c32, n);
   return cudaGetLastError();
 }
 
@@ -69,9 +79,7 @@ static cudaError_t kv_impl(const PlanView& P, void* c64, cudaStream_t st) {
 cudaError_t launch_kernel_vector(const PlanView& P, void* c64, void* c32, cudaStream_t st) {
   cudaError_t e = P.dft ? kv_impl<double2>(P, c64, st) : kv_impl<double>(P, c64, st);
   if (e != cudaSuccess || !c32) return e;
-  if (P.dft) round_kernel<double2, float2><<<16, kThreads, 0, st>>>((const double2*)c64, (float2*)c32, P.N);
-  else round_kernel<double, float><<<16, kThreads, 0, st>>>((const double*)c64, (float*)c32, P.N);
-  return cudaGetLastError();
+  return launch_round(P.dft, c64, c32, P.N, st);
 }
 
 // ---------------------------------------------------- conventional correlation

@@ -1,0 +1,841 @@
+// Large plans (2^14 <= N <= 2^24): the hot path with its length-N vectors in
+// global memory, one instance spread over many CTAs.
+//
+//   * Transforms are four-step.  With N = N1 N2 and the natural index split
+//     as i = i2 + N2 i1 (a row-major N1 x N2 view), the DFT is
+//         X(k1 + N1 k2) = sum_i2 w_N2^(i2 k2) w_N^(i2 k1) sum_i1 x(i2 + N2 i1) w_N1^(i1 k1)
+//     and the Sylvester WHT is H_N = H_N1 (x) H_N2 (no twiddles, output index
+//     k2 + N2 k1).  Pass 1 transforms the columns (length N1, stride N2) in
+//     tiles of adjacent columns and applies w_N^(i2 k1); pass 2 transforms
+//     the rows (length N2, contiguous) in tiles of adjacent rows and writes
+//     natural order.  Both sub-transforms are the shared-memory chains of
+//     cs_transform.cuh; each pass reads and writes N elements once.  The
+//     adjoint is conj(F conj(.)): the conjugations ride on pass 1's loads and
+//     pass 2's stores.
+//   * Pass 2 hands its outputs to a sink: store h and/or keep the CTA's
+//     arg-max (Algorithm 1.1 steps 2-3), the residual y - Phi x on Omega
+//     (step 7), or the kernel vector c (Eq. kernelsum).
+//   * The fast correlation h(j) = h_0(j) - sum_k x_k c(j (-) lambda_k)
+//     (Eq. kernelsumOMP) reads c from L2 (c of N = 2^22 complex64 is 32 MB),
+//     2048 outputs per CTA, and keeps the CTA's arg-max.
+//   * One CTA per instance reduces the arg-max partials, appends the column
+//     with the FP64 inverse-factor update of cs_ls.cuh (step 6, Gram entries
+//     read off c) and tests the halting rule (step 8).
+// The host queues, per iteration t, the correlation (kernel sums, or the
+// forward transform of zf(x), the residual on Omega and the adjoint
+// transform) and then the least squares, all on the caller's stream; a
+// finished instance makes every later kernel of that instance return at
+// once.
+#include <cmath>
+
+#include "cs_internal.h"
+#include "cs_ls.cuh"
+
+namespace csf {
+
+namespace {
+
+constexpr int kLT = 256;                   // threads per CTA of every kernel here
+constexpr int kFastCH = 8;                 // outputs per thread of the fast correlation
+constexpr int kFastTile = kLT * kFastCH;   // outputs per CTA of the fast correlation
+constexpr int kMaxBatchY = 65535;          // instances ride on gridDim.y
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <class E>
+struct LDev {
+  using W = typename FT<E>::W;
+  int N, logN, M, n1, n2, wsh;
+  const int* __restrict__ slot;  // [N] natural order: m if j = Omega_m, else -1
+  const E* __restrict__ tw1;     // DIF twiddles of the N1 chain
+  const E* __restrict__ tw2;     // DIF twiddles of the N2 chain
+  const E* __restrict__ wlo;     // w_N^m, m < 2^wsh
+  const E* __restrict__ whi;     // w_N^(m 2^wsh), m < N / 2^wsh
+  const E* __restrict__ c;       // kernel vector, working precision
+  const W* __restrict__ c64;     // kernel vector, FP64
+};
+
+template <class E>
+LDev<E> ldev(const PlanView& P) {
+  LDev<E> d;
+  d.N = P.N;
+  d.logN = P.logN;
+  d.M = P.M;
+  d.n1 = P.n1;
+  d.n2 = P.n2;
+  d.wsh = P.wsh;
+  d.slot = P.slot;
+  constexpr bool f32 = sizeof(typename FT<E>::R) == 4;
+  const E* t = (const E*)(f32 ? P.lt32 : P.lt64);
+  const int N1 = 1 << P.n1, N2 = 1 << P.n2;
+  d.tw1 = t;
+  d.tw2 = t ? t + N1 : nullptr;
+  d.wlo = t ? t + N1 + N2 : nullptr;
+  d.whi = t ? t + N1 + N2 + (1 << P.wsh) : nullptr;
+  d.c = (const E*)(f32 ? P.c32 : P.c64);
+  d.c64 = (const typename FT<E>::W*)P.c64;
+  return d;
+}
+
+// A pass tile is 32 bytes wide: C = 32 / sizeof(E) adjacent columns (pass 1)
+// or rows (pass 2), one full DRAM sector per tile row.  In shared memory each
+// column / row is a swizzled buffer of its own, 16 bytes apart from the next
+// one's bank pattern.
+template <class E> __host__ __device__ constexpr int tile_c() { return 32 / (int)sizeof(E); }
+template <class E> __host__ __device__ constexpr int log_tile_c() { return ilog2c(32 / (int)sizeof(E)); }
+template <class E> __host__ __device__ inline int lstride(int len) { return len + 16 / (int)sizeof(E); }
+template <class E>
+size_t pass_smem(int len) {
+  using V = typename NormT<E>::V;
+  return al16((size_t)tile_c<E>() * lstride<E>(len) * sizeof(E)) + al16(34 * sizeof(V)) + 34 * sizeof(int);
+}
+
+struct LState {  // per instance, in the workspace
+  int p, done, pad0, pad1;
+  double ynorm2, rn2;
+};
+
+enum { LD_DENSE = 0, LD_ZF = 1, LD_ONES = 2 };
+enum { SK_H = 0, SK_ARG = 1, SK_RES = 2, SK_KV = 3 };
+
+template <class E> __device__ __forceinline__ E one_e();
+template <> __device__ __forceinline__ float one_e<float>() { return 1.f; }
+template <> __device__ __forceinline__ double one_e<double>() { return 1.0; }
+template <> __device__ __forceinline__ float2 one_e<float2>() { return make_float2(1.f, 0.f); }
+template <> __device__ __forceinline__ double2 one_e<double2>() { return make_double2(1.0, 0.0); }
+
+// w_N^m = w_N^(m_hi 2^wsh) w_N^(m_lo), m < N
+template <class E>
+__device__ __forceinline__ E root(const LDev<E>& P, int m) {
+  return mul(__ldg(P.whi + (m >> P.wsh)), __ldg(P.wlo + (m & ((1 << P.wsh) - 1))));
+}
+
+// Forward chain (DIF for DFT, natural order in, digit-reversed out; WHT
+// natural in and out) on buffer gi of the tile, by a group of kLT / C threads.
+template <class E, bool DFT>
+__device__ __forceinline__ void tile_chain(E* buf, int len_log, int stride, const E* tw) {
+  constexpr int C = tile_c<E>(), GS = kLT / C;
+  const int gi = threadIdx.x / GS;
+  const Grp g{(int)threadIdx.x % GS, GS, GS == 32 ? -1 : 1 + gi};
+  E* col = buf + gi * stride;
+  if constexpr (DFT) dft_forward(g, col, len_log, tw);
+  else wht(g, col, len_log);
+}
+
+// CTA-wide arg-max (largest v, lowest j); thread 0 writes the partial.
+template <class V>
+__device__ __forceinline__ void block_partial(V v, int j, V* rv, int* rj, V* out_v, int* out_j) {
+  warp_argmax(v, j);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    rv[w] = v;
+    rj[w] = j;
+  }
+  __syncthreads();
+  if (w == 0) {
+    V vv = lane < (kLT >> 5) ? rv[lane] : (V)-1;
+    int jj = lane < (kLT >> 5) ? rj[lane] : 0x7fffffff;
+    warp_argmax(vv, jj);
+    if (lane == 0) {
+      *out_v = vv;
+      *out_j = vv < (V)0 ? -1 : jj;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- pass 1
+// out[b][k1 N2 + i2] = (w_N^(i2 k1) for DFT) * sum_i1 v(i2 + N2 i1) w_N1^(i1 k1)
+// for the C columns i2 of this CTA, v = in (LD_DENSE, stride in_stride),
+// zf_Omega(in) (LD_ZF, in has M entries per instance) or zf_Omega(1)
+// (LD_ONES); conj_in conjugates v first.
+template <class E, bool DFT, int LD>
+__global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restrict__ in, int64_t in_stride,
+                                                   int conj_in, E* __restrict__ out,
+                                                   const LState* __restrict__ st) {
+  constexpr int C = tile_c<E>(), LC = log_tile_c<E>();
+  extern __shared__ __align__(16) unsigned char sm[];
+  E* buf = (E*)sm;
+  const int64_t b = blockIdx.y;
+  if (st && st[b].done) return;
+  const int n1 = P.n1, n2 = P.n2, N1 = 1 << n1;
+  const int cs = lstride<E>(N1);
+  const int c0 = blockIdx.x * C;
+  const E* src = in ? in + b * in_stride : nullptr;
+  for (int q = threadIdx.x; q < C * N1; q += kLT) {
+    const int c = q & (C - 1), i1 = q >> LC;
+    const int i = c0 + c + (i1 << n2);
+    E v;
+    if constexpr (LD == LD_DENSE) {
+      v = src[i];
+    } else {
+      const int m = __ldg(P.slot + i);
+      if constexpr (LD == LD_ZF) v = m >= 0 ? src[m] : zero<E>();
+      else v = m >= 0 ? one_e<E>() : zero<E>();
+    }
+    if (conj_in) v = conjv(v);
+    buf[c * cs + swz<E>(i1)] = v;
+  }
+  __syncthreads();
+  tile_chain<E, DFT>(buf, n1, cs, P.tw1);
+  __syncthreads();
+  E* dst = out + b * (int64_t)P.N;
+  for (int q = threadIdx.x; q < C * N1; q += kLT) {
+    const int c = q & (C - 1), k1 = q >> LC;
+    E v;
+    if constexpr (DFT) v = mul(buf[c * cs + swz<E>(dif_position(k1, n1))], root(P, (c0 + c) * k1));
+    else v = buf[c * cs + swz<E>(k1)];
+    dst[c0 + c + (k1 << n2)] = v;
+  }
+}
+
+// ----------------------------------------------------------------- pass 2
+// Transforms the C rows k1 of this CTA (T[b][k1 N2 + i2], contiguous) and
+// hands each output v = scl * (conj if conj_out)(X(j)), j natural, to the
+// sink:
+//   SK_H    out[j] = v (if out), arg-max over all j      -> partial
+//   SK_ARG  arg-max over j whose bit is clear in `bits` -> partial
+//   SK_RES  out[j] = y[m] - v where j = Omega_m (other j untouched)
+//   SK_KV   out[j] = v
+// A partial is written to part_v / part_j[b * nparts + blockIdx.x].
+template <class E, bool DFT, int SK>
+__global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restrict__ T, int conj_out,
+                                                   typename FT<E>::R scl, E* __restrict__ out,
+                                                   const E* __restrict__ y, const uint32_t* __restrict__ bits,
+                                                   typename NormT<E>::V* __restrict__ part_v,
+                                                   int* __restrict__ part_j, int nparts,
+                                                   const LState* __restrict__ st) {
+  using V = typename NormT<E>::V;
+  constexpr int C = tile_c<E>(), LC = log_tile_c<E>();
+  extern __shared__ __align__(16) unsigned char sm[];
+  E* buf = (E*)sm;
+  const int64_t b = blockIdx.y;
+  if (st && st[b].done) return;
+  const int n1 = P.n1, n2 = P.n2, N2 = 1 << n2;
+  const int cs = lstride<E>(N2);
+  V* rv = (V*)(sm + al16((size_t)C * cs * sizeof(E)));
+  int* rj = (int*)(sm + al16((size_t)C * cs * sizeof(E)) + al16(34 * sizeof(V)));
+  const int r0 = blockIdx.x * C;
+  const E* src = T + b * (int64_t)P.N;
+  for (int q = threadIdx.x; q < C * N2; q += kLT) {
+    const int c = q >> n2, k = q & (N2 - 1);
+    buf[c * cs + swz<E>(k)] = src[((r0 + c) << n2) + k];
+  }
+  __syncthreads();
+  tile_chain<E, DFT>(buf, n2, cs, P.tw2);
+  __syncthreads();
+  E* dst = out ? out + b * (int64_t)P.N : nullptr;
+  const E* yb = y ? y + b * (int64_t)P.M : nullptr;
+  const uint32_t* bb = bits ? bits + b * (int64_t)(P.N >> 5) : nullptr;
+  V bv = (V)-1;
+  int bj = 0x7fffffff;
+  for (int q = threadIdx.x; q < C * N2; q += kLT) {
+    int c, k2, j, pos;
+    if constexpr (DFT) {  // C adjacent outputs per k2: j = k1 + N1 k2
+      c = q & (C - 1);
+      k2 = q >> LC;
+      j = r0 + c + (k2 << n1);
+      pos = dif_position(k2, n2);
+    } else {              // contiguous rows: j = k2 + N2 k1
+      c = q >> n2;
+      k2 = q & (N2 - 1);
+      j = k2 + ((r0 + c) << n2);
+      pos = k2;
+    }
+    E v = buf[c * cs + swz<E>(pos)];
+    if (conj_out) v = conjv(v);
+    v = scale(v, scl);
+    if constexpr (SK == SK_H || SK == SK_ARG) {
+      if (SK == SK_H && dst) dst[j] = v;
+      if (!bb || !in_bits(bb, j)) {
+        const V a = norm2(v);
+        if (better(a, j, bv, bj)) {
+          bv = a;
+          bj = j;
+        }
+      }
+    } else if constexpr (SK == SK_RES) {
+      const int m = __ldg(P.slot + j);
+      if (m >= 0) dst[j] = sub(yb[m], v);
+    } else {
+      dst[j] = v;
+    }
+  }
+  if constexpr (SK == SK_H || SK == SK_ARG) {
+    if (part_v) block_partial(bv, bj, rv, rj, part_v + b * nparts + blockIdx.x, part_j + b * nparts + blockIdx.x);
+  }
+}
+
+// ------------------------------------------------------ fast correlation
+// h(j) = h0(j) - sum_{k<s} x_k c(j (-) lam_k) for the kFastTile outputs of
+// this CTA (Eq. kernelsumOMP); lam / x of instance b start at b * kstride.
+// Stores h if h != NULL; the arg-max over j with a clear bit (all j if
+// bits == NULL) goes to the partial.
+template <class E, bool DFT>
+__global__ void __launch_bounds__(kLT) lfast_kernel(LDev<E> P, const E* __restrict__ h0,
+                                                    const int* __restrict__ lam, const E* __restrict__ xw, int s,
+                                                    int64_t kstride, const uint32_t* __restrict__ bits,
+                                                    E* __restrict__ h, typename NormT<E>::V* __restrict__ part_v,
+                                                    int* __restrict__ part_j, int nparts,
+                                                    const LState* __restrict__ st) {
+  using V = typename NormT<E>::V;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int64_t b = blockIdx.y;
+  if (st && st[b].done) return;
+  const int N = P.N;
+  E* xs = (E*)sm;
+  int* ls = (int*)(sm + al16((size_t)s * sizeof(E)));
+  V* rv = (V*)(sm + al16((size_t)s * sizeof(E)) + al16((size_t)s * sizeof(int)));
+  int* rj = (int*)((unsigned char*)rv + al16(34 * sizeof(V)));
+  for (int k = threadIdx.x; k < s; k += kLT) {
+    ls[k] = lam[b * kstride + k] & (N - 1);  // reduced mod N: no index leaves c
+    xs[k] = xw[b * kstride + k];
+  }
+  __syncthreads();
+  const int j0 = blockIdx.x * kFastTile + threadIdx.x;
+  const E* hb = h0 + b * (int64_t)N;
+  E acc[kFastCH];
+#pragma unroll
+  for (int e = 0; e < kFastCH; ++e) acc[e] = hb[j0 + e * kLT];
+#pragma unroll 2
+  for (int k = 0; k < s; ++k) {
+    const int l = ls[k];
+    const E xk = xs[k];
+#pragma unroll
+    for (int e = 0; e < kFastCH; ++e) {
+      const int j = j0 + e * kLT;
+      const int d = DFT ? ((j - l) & (N - 1)) : (j ^ l);
+      acc[e] = fnms(acc[e], xk, __ldg(P.c + d));
+    }
+  }
+  const uint32_t* bb = bits ? bits + b * (int64_t)(N >> 5) : nullptr;
+  E* hout = h ? h + b * (int64_t)N : nullptr;
+  V bv = (V)-1;
+  int bj = 0x7fffffff;
+#pragma unroll
+  for (int e = 0; e < kFastCH; ++e) {
+    const int j = j0 + e * kLT;
+    if (hout) hout[j] = acc[e];
+    if (!bb || !in_bits(bb, j)) {
+      const V a = norm2(acc[e]);
+      if (better(a, j, bv, bj)) {
+        bv = a;
+        bj = j;
+      }
+    }
+  }
+  if (part_v) block_partial(bv, bj, rv, rj, part_v + b * nparts + blockIdx.x, part_j + b * nparts + blockIdx.x);
+}
+
+// arg-max of each instance's partials -> amax[b]
+template <class V>
+__global__ void __launch_bounds__(kLT) lreduce_kernel(const V* __restrict__ part_v, const int* __restrict__ part_j,
+                                                      int nparts, int32_t* __restrict__ amax) {
+  __shared__ V rv[34];
+  __shared__ int rj[34];
+  __shared__ V ov;
+  __shared__ int oj;
+  const int64_t b = blockIdx.x;
+  V bv = (V)-1;
+  int bj = 0x7fffffff;
+  for (int i = threadIdx.x; i < nparts; i += kLT) {
+    const V v = part_v[b * nparts + i];
+    const int j = part_j[b * nparts + i];
+    if (v >= (V)0 && better(v, j, bv, bj)) {
+      bv = v;
+      bj = j;
+    }
+  }
+  block_partial(bv, bj, rv, rj, &ov, &oj);
+  __syncthreads();
+  if (threadIdx.x == 0) amax[b] = oj;
+}
+
+// bits[b] <- the set {supp[b][k] mod N}
+__global__ void lbits_kernel(const int32_t* __restrict__ supp, int s, int N, uint32_t* __restrict__ bits) {
+  const int64_t b = blockIdx.x;
+  uint32_t* bb = bits + b * (int64_t)(N >> 5);
+  for (int k = threadIdx.x; k < s; k += blockDim.x) {
+    const int l = supp[b * s + k] & (N - 1);
+    atomicOr(bb + (l >> 5), 1u << (l & 31));
+  }
+}
+
+// w_N^m (m < 2^wsh) and w_N^(m 2^wsh) (m < N / 2^wsh), FP64 by sincospi of an
+// exact argument, rounded to FP32 where asked
+__global__ void roots_kernel(int logN, int wsh, double2* lo64, double2* hi64, float2* lo32, float2* hi32) {
+  const int nlo = 1 << wsh, nhi = 1 << (logN - wsh);
+  const double invN = ldexp(1.0, -logN);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlo + nhi; i += gridDim.x * blockDim.x) {
+    const bool lo = i < nlo;
+    const int m = lo ? i : (i - nlo);
+    const double a = -2.0 * (lo ? (double)m : ldexp((double)m, wsh)) * invN;
+    double sn, cs;
+    sincospi(a, &sn, &cs);
+    if (lo) {
+      lo64[m] = make_double2(cs, sn);
+      if (lo32) lo32[m] = make_float2((float)cs, (float)sn);
+    } else {
+      hi64[m] = make_double2(cs, sn);
+      if (hi32) hi32[m] = make_float2((float)cs, (float)sn);
+    }
+  }
+}
+
+// --------------------------------------------------------- least squares
+template <class E>
+struct LOmpArgs {
+  using W = typename FT<E>::W;
+  using V = typename NormT<E>::V;
+  LDev<E> P;
+  const E* __restrict__ y;
+  int K;
+  double rel_tol;
+  W* x_out;
+  int* supp_out;
+  int* iters_out;
+  double* res_out;
+  E* h0;           // [batch][N]
+  E* xz;           // [batch][N] zero-filled x in the working precision (NULL: kernel sums only)
+  uint32_t* bits;  // [batch][N / 32] support bitmap
+  W* B;            // [batch][K(K+1)/2]
+  W* z;            // [batch][K]
+  W* x;            // [batch][K]
+  E* xw;           // [batch][K]
+  int* lam;        // [batch][K]
+  LState* st;      // [batch]
+  V* part_v;       // [batch][nparts]
+  int* part_j;
+  int nparts;
+};
+
+template <class E>
+struct LLsLayout {
+  size_t g, part, terms, red, rv, rj, total;
+};
+
+template <class E>
+__host__ __device__ inline LLsLayout<E> lls_layout(int K) {
+  using W = typename FT<E>::W;
+  using V = typename NormT<E>::V;
+  LLsLayout<E> L;
+  const int Kc = K > 0 ? K : 1;
+  size_t o = 0;
+  L.g = o;     o = al16(o + (size_t)Kc * sizeof(W));
+  L.part = o;  o = al16(o + (size_t)(2 * kLT > Kc ? 2 * kLT : Kc) * sizeof(W));
+  L.terms = o; o = al16(o + (size_t)3 * Kc * sizeof(double));
+  L.red = o;   o = al16(o + 33 * sizeof(double));
+  L.rv = o;    o = al16(o + 34 * sizeof(V));
+  L.rj = o;    o = al16(o + 34 * sizeof(int));
+  L.total = o;
+  return L;
+}
+
+template <class E>
+__device__ void lwrite_outputs(const LOmpArgs<E>& a, int64_t b, int p, double ynorm2, double rn2) {
+  using W = typename FT<E>::W;
+  const int K = a.K;
+  const W* xb = a.x + b * K;
+  const int* lb = a.lam + b * K;
+  for (int k = threadIdx.x; k < K; k += kLT) {
+    if (a.x_out) a.x_out[b * K + k] = k < p ? xb[k] : W{};
+    a.supp_out[b * K + k] = k < p ? lb[k] : -1;
+  }
+  if (threadIdx.x == 0) {
+    if (a.iters_out) a.iters_out[b] = p;
+    if (a.res_out) a.res_out[b] = ynorm2 > 0.0 ? sqrt(fmax(rn2, 0.0) / ynorm2) : 0.0;
+    a.st[b].done = 1;
+  }
+}
+
+// One iteration's identification (reduction of the partials), least-squares
+// append and halting test for instance blockIdx.x.
+template <class E>
+__global__ void __launch_bounds__(kLT) lls_kernel(LOmpArgs<E> a, int nparts) {
+  using W = typename FT<E>::W;
+  using V = typename NormT<E>::V;
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ LsShared<W> sh;
+  __shared__ double rn2;
+  __shared__ V sel_v;
+  __shared__ int sel_j;
+  const int64_t b = blockIdx.x;
+  LState* S = a.st + b;
+  if (S->done) return;
+  const LLsLayout<E> L = lls_layout<E>(a.K);
+  const Grp g = whole_block();
+  const int N = a.P.N, M = a.P.M, K = a.K;
+  const int p = S->p;
+  double ynorm2 = S->ynorm2;
+  // step 3: the column with the largest |h(j)|^2 over all partials
+  {
+    V bv = (V)-1;
+    int bj = 0x7fffffff;
+    for (int i = threadIdx.x; i < nparts; i += kLT) {
+      const V v = a.part_v[b * a.nparts + i];
+      const int j = a.part_j[b * a.nparts + i];
+      if (v >= (V)0 && better(v, j, bv, bj)) {
+        bv = v;
+        bj = j;
+      }
+    }
+    block_partial(bv, bj, (V*)(sm + L.rv), (int*)(sm + L.rj), &sel_v, &sel_j);
+  }
+  if (p == 0) {  // t = 1: ||y||^2 in FP64
+    double yy[1] = {0.0};
+    const E* yb = a.y + b * M;
+    for (int m = threadIdx.x; m < M; m += kLT) yy[0] += norm2(to_w(yb[m]));
+    group_sum(g, yy, (double*)(sm + L.red));
+    ynorm2 = yy[0];
+    if (!(ynorm2 > 0.0) || K == 0) {  // zero measurement (or K = 0): no iteration
+      lwrite_outputs(a, b, 0, ynorm2, ynorm2);
+      return;
+    }
+    if (threadIdx.x == 0) rn2 = ynorm2;
+  } else if (threadIdx.x == 0) {
+    rn2 = S->rn2;
+  }
+  __syncthreads();
+  const int l = sel_j;
+  if (l < 0) {  // no candidate column left
+    lwrite_outputs(a, b, p, ynorm2, rn2);
+    return;
+  }
+  LsView<E> lv;
+  lv.B = a.B + b * (((int64_t)K * (K + 1)) >> 1);
+  lv.z = a.z + b * K;
+  lv.x = a.x + b * K;
+  lv.g = (W*)(sm + L.g);
+  lv.part = (W*)(sm + L.part);
+  lv.terms = (double*)(sm + L.terms);
+  lv.xw = a.xw + b * K;
+  lv.lam = a.lam + b * K;
+  lv.bits = a.bits + b * (int64_t)(N >> 5);
+  lv.kidx = nullptr;
+  PlanDev<E> pd;
+  pd.N = N;
+  pd.logN = a.P.logN;
+  pd.M = M;
+  pd.slot = a.P.slot;
+  pd.tw = nullptr;
+  pd.c = a.P.c;
+  pd.c64 = a.P.c64;
+  ls_append(g, pd, lv, a.h0 + b * (int64_t)N, p, l, rn2, sh);  // step 6
+  if (sh.st == 1) {                                            // column dependent on Lambda
+    lwrite_outputs(a, b, p, ynorm2, rn2);
+    return;
+  }
+  if (p + 1 >= K || rn2 < a.rel_tol * a.rel_tol * ynorm2) {  // step 8
+    lwrite_outputs(a, b, p + 1, ynorm2, rn2);
+    return;
+  }
+  if (a.xz) {  // zero-filled x for the next transform iteration
+    E* xzb = a.xz + b * (int64_t)N;
+    for (int k = threadIdx.x; k <= p; k += kLT) xzb[lv.lam[k]] = lv.xw[k];
+  }
+  if (threadIdx.x == 0) {
+    S->p = p + 1;
+    S->ynorm2 = ynorm2;
+    S->rn2 = rn2;
+  }
+}
+
+// ------------------------------------------------------------- launchers
+template <class K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <class E, bool DFT, int LD>
+cudaError_t run_col(const LDev<E>& P, const E* in, int64_t in_stride, int conj_in, E* out, const LState* st,
+                    int64_t batch, cudaStream_t s) {
+  const size_t smem = pass_smem<E>(1 << P.n1);
+  cudaError_t e = allow_smem(lcol_kernel<E, DFT, LD>, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((1u << P.n2) / tile_c<E>(), (unsigned)batch);
+  lcol_kernel<E, DFT, LD><<<grid, kLT, smem, s>>>(P, in, in_stride, conj_in, out, st);
+  return cudaGetLastError();
+}
+
+template <class E, bool DFT, int SK>
+cudaError_t run_row(const LDev<E>& P, const E* T, int conj_out, double scl, E* out, const E* y,
+                    const uint32_t* bits, typename NormT<E>::V* pv, int* pj, int nparts, const LState* st,
+                    int64_t batch, cudaStream_t s) {
+  const size_t smem = pass_smem<E>(1 << P.n2);
+  cudaError_t e = allow_smem(lrow_kernel<E, DFT, SK>, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((1u << P.n1) / tile_c<E>(), (unsigned)batch);
+  lrow_kernel<E, DFT, SK><<<grid, kLT, smem, s>>>(P, T, conj_out, (typename FT<E>::R)scl, out, y, bits, pv, pj,
+                                                  nparts, st);
+  return cudaGetLastError();
+}
+
+template <class E, bool DFT>
+cudaError_t run_fast(const LDev<E>& P, const E* h0, const int* lam, const E* xw, int s, int64_t kstride,
+                     const uint32_t* bits, E* h, typename NormT<E>::V* pv, int* pj, int nparts, const LState* st,
+                     int64_t batch, cudaStream_t strm) {
+  using V = typename NormT<E>::V;
+  const size_t smem = al16((size_t)s * sizeof(E)) + al16((size_t)s * sizeof(int)) + al16(34 * sizeof(V)) +
+                      34 * sizeof(int);
+  cudaError_t e = allow_smem(lfast_kernel<E, DFT>, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(P.N / kFastTile, (unsigned)batch);
+  lfast_kernel<E, DFT><<<grid, kLT, smem, strm>>>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st);
+  return cudaGetLastError();
+}
+
+template <class E>
+int row_parts(const LDev<E>& P) { return (1 << P.n1) / tile_c<E>(); }
+template <class E>
+int fast_parts(const LDev<E>& P) { return P.N / kFastTile; }
+
+inline double inv_sqrt_n(int logN) { return 1.0 / std::sqrt(std::ldexp(1.0, logN)); }
+
+// ------------------------------------------------ standalone correlations
+template <class E>
+size_t corr_ws_t(const PlanView& Pv, int64_t batch) {
+  using V = typename NormT<E>::V;
+  const LDev<E> P = ldev<E>(Pv);
+  const int np = row_parts(P);
+  return al16((size_t)batch * P.N * sizeof(E)) + al16((size_t)batch * np * sizeof(V)) +
+         al16((size_t)batch * np * sizeof(int));
+}
+
+template <class E>
+cudaError_t corr_t(const PlanView& Pv, const void* r, int64_t batch, void* h, int32_t* amax, void* ws,
+                   cudaStream_t s) {
+  using V = typename NormT<E>::V;
+  constexpr bool DFT = FT<E>::C;
+  const LDev<E> P = ldev<E>(Pv);
+  const int np = row_parts(P);
+  unsigned char* w = (unsigned char*)ws;
+  E* T = (E*)w;
+  V* pv = (V*)(w + al16((size_t)batch * P.N * sizeof(E)));
+  int* pj = (int*)((unsigned char*)pv + al16((size_t)batch * np * sizeof(V)));
+  cudaError_t e = run_col<E, DFT, LD_ZF>(P, (const E*)r, P.M, DFT, T, nullptr, batch, s);
+  if (e != cudaSuccess) return e;
+  e = run_row<E, DFT, SK_H>(P, T, DFT, inv_sqrt_n(P.logN), (E*)h, nullptr, nullptr, amax ? pv : nullptr,
+                            amax ? pj : nullptr, np, nullptr, batch, s);
+  if (e != cudaSuccess || !amax) return e;
+  lreduce_kernel<V><<<(unsigned)batch, kLT, 0, s>>>(pv, pj, np, amax);
+  return cudaGetLastError();
+}
+
+template <class E>
+size_t fast_ws_t(const PlanView& Pv, int64_t batch) {
+  using V = typename NormT<E>::V;
+  const LDev<E> P = ldev<E>(Pv);
+  const int np = fast_parts(P);
+  return al16((size_t)batch * (P.N >> 5) * sizeof(uint32_t)) + al16((size_t)batch * np * sizeof(V)) +
+         al16((size_t)batch * np * sizeof(int));
+}
+
+template <class E>
+cudaError_t fast_t(const PlanView& Pv, const void* h0, const int32_t* supp, const void* x, int s, int64_t batch,
+                   void* h, int32_t* amax, void* ws, cudaStream_t st) {
+  using V = typename NormT<E>::V;
+  constexpr bool DFT = FT<E>::C;
+  const LDev<E> P = ldev<E>(Pv);
+  const int np = fast_parts(P);
+  unsigned char* w = (unsigned char*)ws;
+  uint32_t* bits = (uint32_t*)w;
+  V* pv = (V*)(w + al16((size_t)batch * (P.N >> 5) * sizeof(uint32_t)));
+  int* pj = (int*)((unsigned char*)pv + al16((size_t)batch * np * sizeof(V)));
+  cudaError_t e = cudaMemsetAsync(bits, 0, (size_t)batch * (P.N >> 5) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  if (s > 0) {
+    lbits_kernel<<<(unsigned)batch, kLT, 0, st>>>(supp, s, P.N, bits);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  e = run_fast<E, DFT>(P, (const E*)h0, supp, (const E*)x, s, s, bits, (E*)h, amax ? pv : nullptr,
+                       amax ? pj : nullptr, np, nullptr, batch, st);
+  if (e != cudaSuccess || !amax) return e;
+  lreduce_kernel<V><<<(unsigned)batch, kLT, 0, st>>>(pv, pj, np, amax);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- OMP
+template <class E>
+struct LOmpWs {
+  size_t st, h0, T, Z, xz, bits, B, z, x, xw, lam, pv, pj, total;
+  int nparts;
+};
+
+template <class E>
+LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
+  using W = typename FT<E>::W;
+  using V = typename NormT<E>::V;
+  const LDev<E> P = ldev<E>(Pv);
+  const bool conv = path != 0;  // CS_PATH_FAST == 0
+  LOmpWs<E> L;
+  const int rp = row_parts(P), fp = fast_parts(P);
+  L.nparts = rp > fp ? rp : fp;
+  const size_t Nv = (size_t)batch * P.N * sizeof(E);
+  const size_t Kc = (size_t)(K > 0 ? K : 1);
+  size_t o = 0;
+  L.st = o;   o = al16(o + (size_t)batch * sizeof(LState));
+  L.h0 = o;   o = al16(o + Nv);
+  L.T = o;    o = al16(o + Nv);
+  L.Z = o;    o = al16(o + (conv ? Nv : 0));
+  L.xz = o;   o = al16(o + (conv ? Nv : 0));
+  L.bits = o; o = al16(o + (size_t)batch * (P.N >> 5) * sizeof(uint32_t));
+  L.B = o;    o = al16(o + (size_t)batch * ((Kc * (Kc + 1)) / 2) * sizeof(W));
+  L.z = o;    o = al16(o + (size_t)batch * Kc * sizeof(W));
+  L.x = o;    o = al16(o + (size_t)batch * Kc * sizeof(W));
+  L.xw = o;   o = al16(o + (size_t)batch * Kc * sizeof(E));
+  L.lam = o;  o = al16(o + (size_t)batch * Kc * sizeof(int));
+  L.pv = o;   o = al16(o + (size_t)batch * L.nparts * sizeof(V));
+  L.pj = o;   o = al16(o + (size_t)batch * L.nparts * sizeof(int));
+  L.total = o;
+  return L;
+}
+
+template <class E>
+cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t s) {
+  using W = typename FT<E>::W;
+  using V = typename NormT<E>::V;
+  constexpr bool DFT = FT<E>::C;
+  const LDev<E> P = ldev<E>(Pv);
+  const int64_t batch = a.batch;
+  const LOmpWs<E> L = lomp_ws<E>(Pv, a.K, a.path, batch);
+  unsigned char* w = (unsigned char*)ws;
+  LOmpArgs<E> A;
+  A.P = P;
+  A.y = (const E*)a.y;
+  A.K = a.K;
+  A.rel_tol = a.rel_tol;
+  A.x_out = (W*)a.x_out;
+  A.supp_out = a.supp_out;
+  A.iters_out = a.iters_out;
+  A.res_out = a.res_out;
+  A.st = (LState*)(w + L.st);
+  A.h0 = (E*)(w + L.h0);
+  E* T = (E*)(w + L.T);
+  E* Z = a.path != 0 ? (E*)(w + L.Z) : nullptr;
+  A.xz = a.path != 0 ? (E*)(w + L.xz) : nullptr;
+  A.bits = (uint32_t*)(w + L.bits);
+  A.B = (W*)(w + L.B);
+  A.z = (W*)(w + L.z);
+  A.x = (W*)(w + L.x);
+  A.xw = (E*)(w + L.xw);
+  A.lam = (int*)(w + L.lam);
+  A.part_v = (V*)(w + L.pv);
+  A.part_j = (int*)(w + L.pj);
+  A.nparts = L.nparts;
+  const size_t Nv = (size_t)batch * P.N * sizeof(E);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(A.st, 0, (size_t)batch * sizeof(LState), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(A.bits, 0, (size_t)batch * (P.N >> 5) * sizeof(uint32_t), s)) != cudaSuccess) return e;
+  if (Z && (e = cudaMemsetAsync(Z, 0, Nv, s)) != cudaSuccess) return e;
+  if (A.xz && (e = cudaMemsetAsync(A.xz, 0, Nv, s)) != cudaSuccess) return e;
+  const size_t ls_smem = lls_layout<E>(a.K).total;
+  if ((e = allow_smem(lls_kernel<E>, ls_smem)) != cudaSuccess) return e;
+  const double isq = inv_sqrt_n(P.logN);
+  const int rp = row_parts(P), fp = fast_parts(P);
+  const int T_end = a.K > 0 ? a.K : 1;
+  for (int t = 1; t <= T_end; ++t) {
+    int np;
+    if (t == 1) {  // h_0 = Phi^H y by one transform (Eq. kernelsumOMP, first case)
+      if ((e = run_col<E, DFT, LD_ZF>(P, A.y, P.M, DFT, T, A.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_row<E, DFT, SK_H>(P, T, DFT, isq, A.h0, nullptr, nullptr, A.part_v, A.part_j, L.nparts, A.st,
+                                     batch, s)) != cudaSuccess)
+        return e;
+      np = rp;
+    } else if (a.path == 0 || (a.path == 2 && t <= a.t_switch)) {  // kernel sums over t - 1 atoms
+      if ((e = run_fast<E, DFT>(P, A.h0, A.lam, A.xw, t - 1, a.K, A.bits, nullptr, A.part_v, A.part_j, L.nparts,
+                                A.st, batch, s)) != cudaSuccess)
+        return e;
+      np = fp;
+    } else {  // r = y - Phi x by a forward transform of zf(x), then h = A^H zf(r)
+      if ((e = run_col<E, DFT, LD_DENSE>(P, A.xz, P.N, 0, T, A.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s)) !=
+          cudaSuccess)
+        return e;
+      if ((e = run_col<E, DFT, LD_DENSE>(P, Z, P.N, DFT, T, A.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_row<E, DFT, SK_ARG>(P, T, DFT, isq, nullptr, nullptr, A.bits, A.part_v, A.part_j, L.nparts,
+                                       A.st, batch, s)) != cudaSuccess)
+        return e;
+      np = rp;
+    }
+    lls_kernel<E><<<(unsigned)batch, kLT, ls_smem, s>>>(A, np);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <class W>
+cudaError_t kv_t(const PlanView& Pv, void* c64, void* tmp, cudaStream_t s) {
+  constexpr bool DFT = FT<W>::C;
+  const LDev<W> P = ldev<W>(Pv);
+  cudaError_t e = run_col<W, DFT, LD_ONES>(P, nullptr, 0, 0, (W*)tmp, nullptr, 1, s);
+  if (e != cudaSuccess) return e;
+  // c = N^{-1} A^H 1_Omega scaled as in Eq. (kernelsum): N^{-1} F^H zf(1)
+  return run_row<W, DFT, SK_KV>(P, (const W*)tmp, DFT, std::ldexp(1.0, -P.logN), (W*)c64, nullptr, nullptr,
+                                nullptr, nullptr, 0, nullptr, 1, s);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ entry points
+cudaError_t large_tables(const PlanView& P, void* lt64, void* lt32, cudaStream_t st) {
+  if (!P.dft) return cudaSuccess;
+  const int N1 = 1 << P.n1, N2 = 1 << P.n2;
+  double2* t64 = (double2*)lt64;
+  float2* t32 = (float2*)lt32;
+  cudaError_t e = launch_twiddles_log(P.n1, t64, t32, st);
+  if (e != cudaSuccess) return e;
+  e = launch_twiddles_log(P.n2, t64 + N1, t32 ? t32 + N1 : nullptr, st);
+  if (e != cudaSuccess) return e;
+  const int nlo = 1 << P.wsh;
+  roots_kernel<<<64, kLT, 0, st>>>(P.logN, P.wsh, t64 + N1 + N2, t64 + N1 + N2 + nlo,
+                                   t32 ? t32 + N1 + N2 : nullptr, t32 ? t32 + N1 + N2 + nlo : nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t large_kernel_vector(const PlanView& P, void* c64, void* c32, void* tmp, cudaStream_t st) {
+  cudaError_t e = P.dft ? kv_t<double2>(P, c64, tmp, st) : kv_t<double>(P, c64, tmp, st);
+  if (e != cudaSuccess || !c32) return e;
+  return launch_round(P.dft, c64, c32, P.N, st);
+}
+
+size_t large_correlate_ws(const PlanView& P, int64_t batch) {
+  if (P.dft) return P.fp32 ? corr_ws_t<float2>(P, batch) : corr_ws_t<double2>(P, batch);
+  return P.fp32 ? corr_ws_t<float>(P, batch) : corr_ws_t<double>(P, batch);
+}
+
+cudaError_t large_correlate(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax, void* ws,
+                            cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  if (batch > kMaxBatchY) return cudaErrorInvalidValue;
+  if (P.dft) return P.fp32 ? corr_t<float2>(P, r, batch, h, amax, ws, st) : corr_t<double2>(P, r, batch, h, amax, ws, st);
+  return P.fp32 ? corr_t<float>(P, r, batch, h, amax, ws, st) : corr_t<double>(P, r, batch, h, amax, ws, st);
+}
+
+size_t large_fast_ws(const PlanView& P, int64_t batch) {
+  if (P.dft) return P.fp32 ? fast_ws_t<float2>(P, batch) : fast_ws_t<double2>(P, batch);
+  return P.fp32 ? fast_ws_t<float>(P, batch) : fast_ws_t<double>(P, batch);
+}
+
+cudaError_t large_correlate_fast(const PlanView& P, const void* h0, const int32_t* supp, const void* x, int s,
+                                 int64_t batch, void* h, int32_t* amax, void* ws, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  if (batch > kMaxBatchY) return cudaErrorInvalidValue;
+  if (P.dft) return P.fp32 ? fast_t<float2>(P, h0, supp, x, s, batch, h, amax, ws, st)
+                           : fast_t<double2>(P, h0, supp, x, s, batch, h, amax, ws, st);
+  return P.fp32 ? fast_t<float>(P, h0, supp, x, s, batch, h, amax, ws, st)
+                : fast_t<double>(P, h0, supp, x, s, batch, h, amax, ws, st);
+}
+
+size_t large_omp_ws(const PlanView& P, int K, int path, int64_t batch) {
+  if (P.dft) return P.fp32 ? lomp_ws<float2>(P, K, path, batch).total : lomp_ws<double2>(P, K, path, batch).total;
+  return P.fp32 ? lomp_ws<float>(P, K, path, batch).total : lomp_ws<double>(P, K, path, batch).total;
+}
+
+cudaError_t large_omp(const PlanView& P, const OmpLaunch& a, void* ws, cudaStream_t st) {
+  if (a.batch <= 0) return cudaSuccess;
+  if (a.batch > kMaxBatchY) return cudaErrorInvalidValue;
+  if (P.dft) return P.fp32 ? omp_t<float2>(P, a, ws, st) : omp_t<double2>(P, a, ws, st);
+  return P.fp32 ? omp_t<float>(P, a, ws, st) : omp_t<double>(P, a, ws, st);
+}
+
+}  // namespace csf

@@ -50,6 +50,10 @@ extern "C" cs_status cs_omp_noalloc(cs_plan_t plan, const void* y_dev, int64_t b
   const PlanView& v = *plan_view(plan);
   if (K > v.M) return CS_ERR_INVALID;
   if (K > kMaxK) return CS_ERR_UNSUPPORTED;
+  if (v.large) {  // the multi-kernel path of N > 8192 keeps per-instance vectors far beyond the array
+    set_last_error("cs_omp_noalloc: plans with N > 8192 are not supported");
+    return CS_ERR_UNSUPPORTED;
+  }
   cs_halt h = {1e-6, CS_PATH_HYBRID, -1, 0};
   if (halt) h = *halt;
   if (!(h.rel_tol >= 0.0) || h.rel_tol > 1e308) return CS_ERR_INVALID;

@@ -49,6 +49,6 @@ def test_host_side_validation_without_gpu():
     assert L.cs_plan_create(16, om3, 1, 1, 1, None, ctypes.byref(h)) == 1
     assert L.cs_plan_create(12, om3, 1, 1, 1, None, ctypes.byref(h)) == 1   # N not a power of two
     assert L.cs_plan_create(16, om3, 17, 1, 1, None, ctypes.byref(h)) == 1  # M > N
-    assert L.cs_plan_create(1 << 14, None, 0, 1, 1, None, ctypes.byref(h)) == 4  # beyond N limit
+    assert L.cs_plan_create(1 << 25, None, 0, 1, 1, None, ctypes.byref(h)) == 4  # beyond N limit (2^24)
     assert L.cs_plan_create(16, None, 0, 2, 1, None, ctypes.byref(h)) == 1   # bad kind
     assert L.cs_omp(None, None, 1, 4, None, None, None, None, None, None) == 1

@@ -1,0 +1,205 @@
+"""Parity of the large-plan path (N > 8192: four-step transforms through
+global memory, kernel sums from L2, one least-squares CTA per instance)
+with the FP64 oracle, through the C ABI.
+
+Tolerances as for the one-CTA path: h within 1e-12 relative (FP64) or 2e-5
+(FP32, l_inf / ||h||_inf); supports bit-exact up to the first iteration whose
+oracle top-two gap is at most 1e-3; x within 1e-10 (FP64) or 1e-4 (FP32)
+relative in noiseless cases.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import kernelsum, transform as tro
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1205_4139_gb300 import binding  # noqa: E402
+
+TOL_H = {"fp64": 1e-12, "fp32": 2e-5}
+TOL_X = {"fp64": 1e-10, "fp32": 1e-4}
+MODES = [("wht", "fp64"), ("wht", "fp32"), ("dft", "fp64"), ("dft", "fp32")]
+
+
+def rel_inf(a, b):
+    den = np.max(np.abs(b))
+    return np.max(np.abs(a - b)) / (den if den > 0 else 1.0)
+
+
+def rand_work(rng, shape, kind, prec):
+    v = rng.standard_normal(shape) + (1j * rng.standard_normal(shape) if kind == "dft" else 0)
+    return v.astype(synth.working_dtype(kind, prec))
+
+
+@pytest.mark.parametrize("kind,prec", MODES)
+@pytest.mark.parametrize("N,M", [(1 << 14, 3000), (1 << 15, 4096), (1 << 17, 9999)])
+def test_large_kernel_vector(kind, prec, N, M):
+    om = synth.draw_omega(N, M, np.random.default_rng(N + M))
+    plan = binding.Plan(N, om, kind, prec)
+    c = plan.kernel_vector("fp64").cpu().numpy()
+    want = tro.kernel_vector(kind, N, om)
+    assert np.max(np.abs(c - want)) < 1e-13
+    if kind == "wht":  # N c is an exact integer: the four-step WHT adds integers only
+        assert np.array_equal(N * c, np.round(N * want))
+    c32 = plan.kernel_vector("fp32").cpu().numpy()
+    assert np.max(np.abs(c32 - want)) < 1e-7
+
+
+@pytest.mark.parametrize("kind,prec", MODES)
+@pytest.mark.parametrize("N,M", [(1 << 14, 4096), (1 << 15, 1000), (1 << 18, 30000)])
+def test_large_correlate(kind, prec, N, M):
+    rng = np.random.default_rng(N ^ M)
+    om = synth.draw_omega(N, M, rng)
+    plan = binding.Plan(N, om, kind, prec)
+    r = rand_work(rng, (3, M), kind, prec)
+    h, am = plan.correlate(torch.from_numpy(r).cuda())
+    h = h.cpu().numpy()
+    am = am.cpu().numpy()
+    for b in range(3):
+        want = tro.correlate(kind, N, om, r[b].astype(np.complex128 if kind == "dft" else np.float64))
+        assert rel_inf(h[b], want) < TOL_H[prec]
+        s = np.abs(want) ** 2
+        top = np.sort(s)[-2:]
+        if (np.sqrt(top[1]) - np.sqrt(top[0])) / np.sqrt(top[1]) > 1e-3:
+            assert am[b] == int(np.argmax(s))
+        else:
+            assert s[am[b]] >= top[0] * (1 - 1e-3)
+
+
+@pytest.mark.parametrize("kind,prec", MODES)
+@pytest.mark.parametrize("N,s", [(1 << 14, 0), (1 << 14, 37), (1 << 16, 200)])
+def test_large_correlate_fast(kind, prec, N, s):
+    rng = np.random.default_rng(N + s)
+    M = N // 4
+    om = synth.draw_omega(N, M, rng)
+    plan = binding.Plan(N, om, kind, prec)
+    c = tro.kernel_vector(kind, N, om)
+    h0 = rand_work(rng, (2, N), kind, prec)
+    supp = np.stack([rng.choice(N, s, replace=False) for _ in range(2)]).astype(np.int32).reshape(2, s)
+    x = rand_work(rng, (2, s), kind, prec)
+    h, am = plan.correlate_fast(torch.from_numpy(h0).cuda(), torch.from_numpy(supp).cuda(),
+                                torch.from_numpy(x).cuda())
+    h = h.cpu().numpy()
+    am = am.cpu().numpy()
+    wt = np.complex128 if kind == "dft" else np.float64
+    for b in range(2):
+        want = kernelsum.fast_correlation(kind, N, c, h0[b].astype(wt), supp[b], x[b].astype(wt))
+        assert rel_inf(h[b], want) < TOL_H[prec]
+        sc = np.abs(want) ** 2
+        sc[supp[b]] = -1
+        j = int(np.argmax(sc))
+        ss = np.sort(sc)[-2:]
+        if (np.sqrt(ss[1]) - np.sqrt(max(ss[0], 0))) / np.sqrt(ss[1]) > 1e-3:
+            assert am[b] == j
+        assert am[b] not in set(supp[b].tolist())
+
+
+def check_omp(kind, prec, inst, x, supp, iters, res, noiseless):
+    N, K = inst["N"], inst["K"]
+    x = x.cpu().numpy()
+    supp = supp.cpu().numpy()
+    iters = iters.cpu().numpy()
+    res = res.cpu().numpy()
+    wt = np.complex128 if kind == "dft" else np.float64
+    compared = 0
+    for b in range(inst["B"]):
+        ref = tro.omp(kind, N, inst["omega"], inst["Y"][b].astype(wt), K)
+        gaps = ref["gap"]
+        upto = next((t for t, g in enumerate(gaps) if g <= 1e-3), len(gaps))
+        assert supp[b][:upto].tolist() == ref["support"][:upto]
+        if upto < len(gaps):
+            continue
+        compared += 1
+        assert iters[b] == ref["iters"] or (prec == "fp32" and ref["halt"] == "tolerance")
+        if noiseless and ref["halt"] != "dependent":
+            xr = np.asarray(ref["x"])
+            n = min(iters[b], len(xr))
+            assert np.max(np.abs(x[b][:n] - xr[:n])) < TOL_X[prec] * np.max(np.abs(xr))
+        if ref["resnorm"]:
+            rr = ref["resnorm"][-1] / ref["ynorm"]
+            # FP64: the downdate resolves ||r||/||y|| to ~1e-8; FP32: the
+            # right-hand side h_0 carries FP32 rounding, so ~1e-3 absolute
+            tol_r = 1e-6 * rr + 1e-7 if prec == "fp64" else max(1e-3 * rr, 1e-3)
+            assert abs(res[b] - rr) <= tol_r
+    return compared
+
+
+@pytest.mark.parametrize("kind,prec", MODES)
+@pytest.mark.parametrize("path", ["fast", "conv", "hybrid"])
+@pytest.mark.parametrize("N,M,K,snr", [(1 << 14, 2048, 24, None), (1 << 15, 3000, 40, 40)])
+def test_large_omp(kind, prec, path, N, M, K, snr):
+    inst = synth.make_batch(kind, N, M, K, 3, snr_db=snr, prec=prec, seed=N + K)
+    plan = binding.Plan(N, inst["omega"], kind, prec)
+    y = torch.from_numpy(inst["Y"]).cuda()
+    x, supp, iters, res = plan.omp(y, K, path=path, t_switch=7)
+    torch.cuda.synchronize()
+    assert check_omp(kind, prec, inst, x, supp, iters, res, snr is None) >= 2
+
+
+@pytest.mark.parametrize("kind,prec", [("dft", "fp64"), ("wht", "fp32")])
+def test_large_paths_agree(kind, prec):
+    N, M, K = 1 << 16, 6000, 48
+    inst = synth.make_batch(kind, N, M, K, 4, snr_db=40, prec=prec, seed=9)
+    plan = binding.Plan(N, inst["omega"], kind, prec)
+    y = torch.from_numpy(inst["Y"]).cuda()
+    outs = {p: plan.omp(y, K, path=p, t_switch=20) for p in ("fast", "conv", "hybrid")}
+    torch.cuda.synchronize()
+    s_fast = outs["fast"][1].cpu().numpy()
+    for p in ("conv", "hybrid"):
+        s = outs[p][1].cpu().numpy()
+        for b in range(4):
+            # the three correlations agree to rounding: supports agree until a near tie
+            ro = tro.omp(kind, N, inst["omega"], inst["Y"][b].astype(np.complex128 if kind == "dft" else np.float64),
+                         K)
+            upto = next((t for t, g in enumerate(ro["gap"]) if g <= 1e-3), len(ro["gap"]))
+            assert s[b][:upto].tolist() == s_fast[b][:upto].tolist() == ro["support"][:upto]
+
+
+@pytest.mark.parametrize("kind,prec", MODES)
+def test_large_edge_cases(kind, prec):
+    N, M = 1 << 14, 1024
+    inst = synth.make_batch(kind, N, M, 12, 3, snr_db=None, prec=prec, seed=4)
+    Y = inst["Y"].copy()
+    Y[1] = 0  # a zero measurement halts before the first iteration
+    plan = binding.Plan(N, inst["omega"], kind, prec)
+    y = torch.from_numpy(Y).cuda()
+    x, supp, iters, res = plan.omp(y, 12)
+    it = iters.cpu().numpy()
+    assert it[1] == 0 and res.cpu().numpy()[1] == 0.0
+    assert (supp.cpu().numpy()[1] == -1).all()
+    assert sorted(supp.cpu().numpy()[0].tolist()) == sorted(inst["support"][0].tolist())
+    # K = 0: no iteration; K = 1: the arg-max of h_0
+    x0, s0, i0, r0 = plan.omp(y, 0)
+    assert (i0.cpu().numpy() == 0).all()
+    x1, s1, i1, r1 = plan.omp(y, 1)
+    h, am = plan.correlate(y)
+    assert s1.cpu().numpy()[0, 0] == am.cpu().numpy()[0] and i1.cpu().numpy()[1] == 0
+    assert plan.device_error() == 0
+
+
+def test_large_big_dft_sampled():
+    """N = 2^20, M = 2^17 complex64 (a large single instance): h_0 at sampled
+    j against the defining sum over Omega, and OMP against the transform
+    oracle."""
+    N, M, K = 1 << 20, 1 << 17, 10
+    inst = synth.make_batch("dft", N, M, K, 1, snr_db=30, prec="fp32", seed=20)
+    plan = binding.Plan(N, inst["omega"], "dft", "fp32")
+    y = torch.from_numpy(inst["Y"]).cuda()
+    h, am = plan.correlate(y)
+    h = h.cpu().numpy()[0]
+    om = inst["omega"].astype(np.int64)
+    yv = inst["Y"][0].astype(np.complex128)
+    js = np.random.default_rng(0).choice(N, 16, replace=False)
+    for j in js:
+        want = np.sum(yv * np.exp(2j * np.pi * ((om * j) % N) / N)) / np.sqrt(N)
+        assert abs(h[j] - want) < 2e-5 * np.max(np.abs(h))
+    x, supp, iters, res = plan.omp(y, K)
+    ref = tro.omp("dft", N, inst["omega"], yv, K)
+    upto = next((t for t, g in enumerate(ref["gap"]) if g <= 1e-3), len(ref["gap"]))
+    assert supp.cpu().numpy()[0][:upto].tolist() == ref["support"][:upto]
+    assert plan.device_error() == 0
