@@ -44,7 +44,7 @@ def test_tune_then_default_switch(kind, prec, N, M, K):
         ref = oomp.omp(Phi, inst["Y"][b].astype(np.complex128 if kind == "dft" else np.float64), K)
         if min(ref["gap"]) <= 1e-3:
             continue
-        assert supp[b][: ref["iters"]].tolist() == ref["support"].tolist()
+        assert supp[b][: ref["iters"]].tolist() == list(ref["support"])
         checked += 1
     assert checked >= 5
 
