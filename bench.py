@@ -8,7 +8,9 @@ initial transform, K identifications with the fast and/or transform
 correlation (hybrid switch), K FP64 least-squares updates, all in one
 persistent kernel.  Inputs are synthetic and seeded; they stay resident in
 HBM for the device-timed value, and go host -> device -> host every step for
-the end-to-end value.  L2 is flushed (a 256 MB write) before every timed step.
+the end-to-end value.  L2 is flushed before every timed step: a 256 MB write,
+then a read of the same buffer, so that the dirty lines of the write are
+written back before the timed region starts instead of inside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -143,6 +145,13 @@ def correlation_flops(N: int, iters: np.ndarray, t_switch: int, path: str) -> fl
     return total
 
 
+def flush_l2(buf):
+    """Evicts L2: write a buffer twice the L2 size, then read it, leaving L2
+    full of clean lines that belong to no input of the timed step."""
+    buf.zero_()
+    buf.sum()
+
+
 def _events_ms(fn, steps, warmup, stream, flush=None):
     import torch
     for _ in range(warmup):
@@ -151,7 +160,7 @@ def _events_ms(fn, steps, warmup, stream, flush=None):
     out = []
     for _ in range(steps):
         if flush is not None:
-            flush.zero_()
+            flush_l2(flush)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         fn()
@@ -212,6 +221,54 @@ def secondary(args, dev, plan, inst, stream, flush):
     out["cosamp_M64_N8192_K4"] = {"ms_per_instance_iteration": per_it,
                                   "fast_over_conv": per_it["fast"] / per_it["conv"],
                                   "paper_flop_model": costmodel.cosamp_fast_ratio(8192, 4)}
+    out["large_dft_c64_N4194304_M524288"] = large_single(dev, stream, flush)
+    return out
+
+
+def large_single(dev, stream, flush, N=1 << 22, M=1 << 19, K=256):
+    """One large partial-DFT complex64 instance (30 dB, N = 2^22, M = 2^19,
+    K = 256): the transform h_0 = Phi^H y against the HBM roofline, the
+    kernel-sum correlation at several support sizes s against L2 traffic,
+    and OMP by each path (transforms four-step through global memory)."""
+    import torch
+    from paper_1205_4139_gb300 import binding
+    inst = synth.make_batch("dft", N, M, K, 1, snr_db=30, prec="fp32", seed=5)
+    t0 = time.perf_counter()
+    plan = binding.Plan(N, inst["omega"], "dft", "fp32")
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    y = torch.from_numpy(inst["Y"]).to(dev)
+    hbm = json.load(open(PEAKS_FILE))["hbm_gbs"] if os.path.exists(PEAKS_FILE) else 6800.0
+    out = {"plan_ms": plan_ms, "hbm_peak_gbs": hbm}
+    h = torch.empty(1, N, dtype=torch.complex64, device=dev)
+    am = torch.empty(1, dtype=torch.int32, device=dev)
+    ms = statistics.median(_events_ms(lambda: plan.correlate(y), 20, 3, stream, flush))
+    # two passes, each reads and writes N complex64; pass 1 also reads the
+    # slot map (4 B per position) and y
+    byts = 2 * 2 * 8 * N + 4 * N + 8 * M
+    out["transform_h0"] = {"ms": ms, "bytes": byts, "gbs": byts / ms / 1e6, "frac_of_hbm": byts / ms / 1e6 / hbm}
+    rng = np.random.default_rng(1)
+    fast = {}
+    for s_ in (8, 32, 128):
+        sp = torch.from_numpy(rng.choice(N, s_, replace=False).astype(np.int32)[None]).to(dev)
+        xs = torch.from_numpy((rng.standard_normal(s_) + 1j * rng.standard_normal(s_)).astype(np.complex64)[None]).to(dev)
+        ms = statistics.median(_events_ms(lambda: plan.correlate_fast(h, sp, xs, want_h=False), 20, 3, stream, flush))
+        l2 = (s_ + 1) * 8 * N
+        fast[str(s_)] = {"ms": ms, "l2_gbs": l2 / ms / 1e6, "gcmac_per_s": s_ * N / ms / 1e6}
+    out["kernel_sums"] = fast
+    x = torch.empty(1, K, dtype=torch.complex128, device=dev)
+    sp = torch.empty(1, K, dtype=torch.int32, device=dev)
+    it = torch.empty(1, dtype=torch.int32, device=dev)
+    rn = torch.empty(1, dtype=torch.float64, device=dev)
+    omp = {}
+    for path in ("fast", "conv"):
+        omp[path] = statistics.median(_events_ms(lambda: plan.omp_into(y, K, x, sp, it, rn, path=path), 3, 1, stream))
+    t_best, curve = plan.tune(y, K)
+    omp["hybrid_tuned"] = statistics.median(_events_ms(lambda: plan.omp_into(y, K, x, sp, it, rn, path="hybrid"), 3, 1,
+                                                       stream))
+    out["omp_ms"] = omp
+    out["t_switch"] = t_best
+    out["t_switch_curve_ms"] = {str(k): round(v, 3) for k, v in curve.items()}
+    out["iters"] = int(it.item())
     return out
 
 
@@ -246,7 +303,7 @@ def run_gpu(args, rank: int, world: int):
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for e0, e1 in ev:
-            flush.zero_()
+            flush_l2(flush)
             e0.record(stream)
             step(path, ts)
             e1.record(stream)
@@ -287,7 +344,7 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.synchronize()
     e2e_ev = []
     for _ in range(max(10, args.steps // 4)):
-        flush.zero_()
+        flush_l2(flush)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         e2e_step()
@@ -392,7 +449,7 @@ def main():
                 "data": "synthetic (seeded)",
                 "config": {"workload": WORKLOAD, "kind": "dft", "N": 4096, "M": 1024, "K": 64,
                            "batch_per_gpu": 1024, "snr_db": 40, "path": "hybrid", "t_switch": r["t_switch"],
-                           "l2": "flushed (256 MB write) before every timed step"},
+                           "l2": "flushed (256 MB write, then read) before every timed step"},
                 "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "correlations_per_s": r["correlations_per_s"],
                 "fast": r["fast"], "conv": r["conv"], "plan_ms": r["plan_ms"],
                 "t_switch_default": r["t_switch_default"], "t_switch_sweep_ms": r["t_switch_sweep_ms"],

@@ -9,9 +9,9 @@
 //     tiles of adjacent columns and applies w_N^(i2 k1); pass 2 transforms
 //     the rows (length N2, contiguous) in tiles of adjacent rows and writes
 //     natural order.  Both sub-transforms are the shared-memory chains of
-//     cs_transform.cuh; each pass reads and writes N elements once.  The
-//     adjoint is conj(F conj(.)): the conjugations ride on pass 1's loads and
-//     pass 2's stores.
+//     cs_transform.cuh; each pass reads and writes N elements once.  Only F
+//     is computed: the adjoint is read off it by negating the output index,
+//     (F^H v)(j) = (F v)(-j mod N), in pass 2's sink.
 //   * Pass 2 hands its outputs to a sink: store h and/or keep the CTA's
 //     arg-max (Algorithm 1.1 steps 2-3), the residual y - Phi x on Omega
 //     (step 7), or the kernel vector c (Eq. kernelsum).
@@ -28,8 +28,8 @@
 // once.
 #include <cmath>
 
+#include "cs_blocks.cuh"
 #include "cs_internal.h"
-#include "cs_ls.cuh"
 
 namespace csf {
 
@@ -39,6 +39,7 @@ constexpr int kLT = 256;                   // threads per CTA of every kernel he
 constexpr int kFastCH = 8;                 // outputs per thread of the fast correlation
 constexpr int kFastTile = kLT * kFastCH;   // outputs per CTA of the fast correlation
 constexpr int kMaxBatchY = 65535;          // instances ride on gridDim.y
+constexpr int kU = 8;                      // independent accesses per thread in flight in the pass loops
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -84,11 +85,6 @@ LDev<E> ldev(const PlanView& P) {
 template <class E> __host__ __device__ constexpr int tile_c() { return 32 / (int)sizeof(E); }
 template <class E> __host__ __device__ constexpr int log_tile_c() { return ilog2c(32 / (int)sizeof(E)); }
 template <class E> __host__ __device__ inline int lstride(int len) { return len + 16 / (int)sizeof(E); }
-template <class E>
-size_t pass_smem(int len) {
-  using V = typename NormT<E>::V;
-  return al16((size_t)tile_c<E>() * lstride<E>(len) * sizeof(E)) + al16(34 * sizeof(V)) + 34 * sizeof(int);
-}
 
 struct LState {  // per instance, in the workspace
   int p, done, pad0, pad1;
@@ -143,15 +139,65 @@ __device__ __forceinline__ void block_partial(V v, int j, V* rv, int* rj, V* out
   }
 }
 
+// ------------------------------------------------------- pass scaffolding
+// Shared memory of a pass CTA: the C swizzled buffers, the digit-reversal
+// table of the sub-transform (DFT), the arg-max scratch.
+template <class E>
+struct PassSmem {
+  size_t tab, red, rv, rj, total;
+};
+template <class E>
+__host__ __device__ inline PassSmem<E> pass_layout(int len) {
+  using V = typename NormT<E>::V;
+  PassSmem<E> L;
+  L.tab = al16((size_t)tile_c<E>() * lstride<E>(len) * sizeof(E));
+  L.red = L.tab + al16((size_t)len * sizeof(short));
+  L.rv = L.red + al16((kLT / 32) * sizeof(double));
+  L.rj = L.rv + al16(34 * sizeof(V));
+  L.total = L.rj + 34 * sizeof(int);
+  return L;
+}
+
+// CTA-wide FP64 sum; thread 0 gets the total (fixed order: deterministic).
+__device__ __forceinline__ double block_sum0(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kLT / 32; ++w) t += red[w];
+  return t;
+}
+
+// One element, global -> shared, without passing through registers
+// (cp.async: 4, 8 or 16 bytes), so that a thread keeps all of its tile's
+// copies in flight at once.
+template <class E>
+__device__ __forceinline__ void cp_async_elem(E* sdst, const E* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gsrc), "n"((int)sizeof(E)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// tab[k] = position of frequency k after the forward DIF chain of length 2^lg
+__device__ __forceinline__ void build_position_table(short* tab, int lg) {
+  for (int k = threadIdx.x; k < (1 << lg); k += kLT) tab[k] = (short)dif_position(k, lg);
+}
+
 // ----------------------------------------------------------------- pass 1
 // out[b][k1 N2 + i2] = (w_N^(i2 k1) for DFT) * sum_i1 v(i2 + N2 i1) w_N1^(i1 k1)
 // for the C columns i2 of this CTA, v = in (LD_DENSE, stride in_stride),
 // zf_Omega(in) (LD_ZF, in has M entries per instance) or zf_Omega(1)
-// (LD_ONES); conj_in conjugates v first.
+// (LD_ONES).  Only the forward transform F is computed here: the adjoint is
+// read off it by index negation in pass 2.  With LD_ZF and ynorm != NULL the
+// CTA also leaves the FP64 sum of |in_m|^2 over the entries it loaded in
+// ynorm[b * gridDim.x + blockIdx.x] (every m is loaded by exactly one CTA).
 template <class E, bool DFT, int LD>
 __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restrict__ in, int64_t in_stride,
-                                                   int conj_in, E* __restrict__ out,
-                                                   const LState* __restrict__ st) {
+                                                   E* __restrict__ out, const LState* __restrict__ st,
+                                                   double* __restrict__ ynorm) {
   constexpr int C = tile_c<E>(), LC = log_tile_c<E>();
   extern __shared__ __align__(16) unsigned char sm[];
   E* buf = (E*)sm;
@@ -159,46 +205,88 @@ __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restric
   if (st && st[b].done) return;
   const int n1 = P.n1, n2 = P.n2, N1 = 1 << n1;
   const int cs = lstride<E>(N1);
+  const PassSmem<E> L = pass_layout<E>(N1);
+  short* tab = (short*)(sm + L.tab);
   const int c0 = blockIdx.x * C;
   const E* src = in ? in + b * in_stride : nullptr;
-  for (int q = threadIdx.x; q < C * N1; q += kLT) {
-    const int c = q & (C - 1), i1 = q >> LC;
-    const int i = c0 + c + (i1 << n2);
-    E v;
-    if constexpr (LD == LD_DENSE) {
-      v = src[i];
-    } else {
-      const int m = __ldg(P.slot + i);
-      if constexpr (LD == LD_ZF) v = m >= 0 ? src[m] : zero<E>();
-      else v = m >= 0 ? one_e<E>() : zero<E>();
+  // C * N1 is a multiple of kLT, so every guard below is uniform per step
+  const int tot = C * N1;
+  if constexpr (LD == LD_DENSE) {
+    for (int q = threadIdx.x; q < tot; q += kLT)
+      cp_async_elem(buf + (q & (C - 1)) * cs + swz<E>(q >> LC), src + c0 + (q & (C - 1)) + ((q >> LC) << n2));
+  } else {  // zero-filled gathers through the slot map, kU in flight per thread
+    double yy = 0.0;
+    for (int q0 = threadIdx.x; q0 < tot; q0 += kU * kLT) {
+      int m[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int q = q0 + u * kLT;
+        m[u] = q < tot ? __ldg(P.slot + c0 + (q & (C - 1)) + ((q >> LC) << n2)) : -1;
+      }
+      E v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if constexpr (LD == LD_ZF) {
+          v[u] = m[u] >= 0 ? src[m[u]] : zero<E>();
+          if (ynorm) yy += norm2(to_w(v[u]));
+        } else {
+          v[u] = m[u] >= 0 ? one_e<E>() : zero<E>();
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int q = q0 + u * kLT;
+        if (q < tot) buf[(q & (C - 1)) * cs + swz<E>(q >> LC)] = v[u];
+      }
     }
-    if (conj_in) v = conjv(v);
-    buf[c * cs + swz<E>(i1)] = v;
+    if constexpr (LD == LD_ZF) {
+      if (ynorm) {
+        const double t = block_sum0(yy, (double*)(sm + L.red));
+        if (threadIdx.x == 0) ynorm[b * gridDim.x + blockIdx.x] = t;
+      }
+    }
   }
+  if constexpr (DFT) build_position_table(tab, n1);
+  if constexpr (LD == LD_DENSE) cp_async_wait_all();
   __syncthreads();
   tile_chain<E, DFT>(buf, n1, cs, P.tw1);
   __syncthreads();
   E* dst = out + b * (int64_t)P.N;
-  for (int q = threadIdx.x; q < C * N1; q += kLT) {
-    const int c = q & (C - 1), k1 = q >> LC;
-    E v;
-    if constexpr (DFT) v = mul(buf[c * cs + swz<E>(dif_position(k1, n1))], root(P, (c0 + c) * k1));
-    else v = buf[c * cs + swz<E>(k1)];
-    dst[c0 + c + (k1 << n2)] = v;
+  for (int q0 = threadIdx.x; q0 < tot; q0 += kU * kLT) {
+    E v[kU], w[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int q = q0 + u * kLT;
+      const int c = q & (C - 1), k1 = q >> LC;
+      if (q < tot) {
+        if constexpr (DFT) {
+          v[u] = buf[c * cs + swz<E>(tab[k1])];
+          w[u] = root(P, (c0 + c) * k1);
+        } else {
+          v[u] = buf[c * cs + swz<E>(k1)];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int q = q0 + u * kLT;
+      if (q < tot) dst[c0 + (q & (C - 1)) + ((q >> LC) << n2)] = DFT ? mul(v[u], w[u]) : v[u];
+    }
   }
 }
 
 // ----------------------------------------------------------------- pass 2
-// Transforms the C rows k1 of this CTA (T[b][k1 N2 + i2], contiguous) and
-// hands each output v = scl * (conj if conj_out)(X(j)), j natural, to the
-// sink:
+// Transforms the C rows k1 of this CTA (T[b][k1 N2 + i2], contiguous): the
+// forward output X(jf), jf natural, is the adjoint's output at j = -jf mod N
+// when neg is set (F^H v (j) = F v (-j), DFT), else at j = jf.  Each output
+// v = scl * X is handed to the sink:
 //   SK_H    out[j] = v (if out), arg-max over all j      -> partial
 //   SK_ARG  arg-max over j whose bit is clear in `bits` -> partial
 //   SK_RES  out[j] = y[m] - v where j = Omega_m (other j untouched)
 //   SK_KV   out[j] = v
 // A partial is written to part_v / part_j[b * nparts + blockIdx.x].
 template <class E, bool DFT, int SK>
-__global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restrict__ T, int conj_out,
+__global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restrict__ T, int neg,
                                                    typename FT<E>::R scl, E* __restrict__ out,
                                                    const E* __restrict__ y, const uint32_t* __restrict__ bits,
                                                    typename NormT<E>::V* __restrict__ part_v,
@@ -210,16 +298,19 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
   E* buf = (E*)sm;
   const int64_t b = blockIdx.y;
   if (st && st[b].done) return;
-  const int n1 = P.n1, n2 = P.n2, N2 = 1 << n2;
+  const int n1 = P.n1, n2 = P.n2, N2 = 1 << n2, Nm = P.N - 1;
   const int cs = lstride<E>(N2);
-  V* rv = (V*)(sm + al16((size_t)C * cs * sizeof(E)));
-  int* rj = (int*)(sm + al16((size_t)C * cs * sizeof(E)) + al16(34 * sizeof(V)));
+  const PassSmem<E> L = pass_layout<E>(N2);
+  short* tab = (short*)(sm + L.tab);
+  V* rv = (V*)(sm + L.rv);
+  int* rj = (int*)(sm + L.rj);
   const int r0 = blockIdx.x * C;
   const E* src = T + b * (int64_t)P.N;
-  for (int q = threadIdx.x; q < C * N2; q += kLT) {
-    const int c = q >> n2, k = q & (N2 - 1);
-    buf[c * cs + swz<E>(k)] = src[((r0 + c) << n2) + k];
-  }
+  const int tot = C * N2;  // a multiple of kLT
+  for (int q = threadIdx.x; q < tot; q += kLT)
+    cp_async_elem(buf + (q >> n2) * cs + swz<E>(q & (N2 - 1)), src + ((r0 + (q >> n2)) << n2) + (q & (N2 - 1)));
+  if constexpr (DFT) build_position_table(tab, n2);
+  cp_async_wait_all();
   __syncthreads();
   tile_chain<E, DFT>(buf, n2, cs, P.tw2);
   __syncthreads();
@@ -228,36 +319,55 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
   const uint32_t* bb = bits ? bits + b * (int64_t)(P.N >> 5) : nullptr;
   V bv = (V)-1;
   int bj = 0x7fffffff;
-  for (int q = threadIdx.x; q < C * N2; q += kLT) {
-    int c, k2, j, pos;
-    if constexpr (DFT) {  // C adjacent outputs per k2: j = k1 + N1 k2
-      c = q & (C - 1);
-      k2 = q >> LC;
-      j = r0 + c + (k2 << n1);
-      pos = dif_position(k2, n2);
-    } else {              // contiguous rows: j = k2 + N2 k1
-      c = q >> n2;
-      k2 = q & (N2 - 1);
-      j = k2 + ((r0 + c) << n2);
-      pos = k2;
-    }
-    E v = buf[c * cs + swz<E>(pos)];
-    if (conj_out) v = conjv(v);
-    v = scale(v, scl);
-    if constexpr (SK == SK_H || SK == SK_ARG) {
-      if (SK == SK_H && dst) dst[j] = v;
-      if (!bb || !in_bits(bb, j)) {
-        const V a = norm2(v);
-        if (better(a, j, bv, bj)) {
-          bv = a;
-          bj = j;
-        }
+  for (int q0 = threadIdx.x; q0 < tot; q0 += kU * kLT) {
+    E v[kU];
+    int jj[kU], aux[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {  // shared reads and the per-output lookups, all issued first
+      const int q = q0 + u * kLT;
+      int c, pos, jf;
+      if constexpr (DFT) {  // C adjacent outputs per k2: jf = k1 + N1 k2
+        c = q & (C - 1);
+        const int k2 = q >> LC;
+        jf = r0 + c + (k2 << n1);
+        pos = q < tot ? tab[k2] : 0;
+      } else {              // contiguous rows: jf = k2 + N2 k1
+        c = q >> n2;
+        pos = q & (N2 - 1);
+        jf = pos + ((r0 + c) << n2);
       }
-    } else if constexpr (SK == SK_RES) {
-      const int m = __ldg(P.slot + j);
-      if (m >= 0) dst[j] = sub(yb[m], v);
-    } else {
-      dst[j] = v;
+      jj[u] = neg ? ((P.N - jf) & Nm) : jf;
+      aux[u] = 0;
+      if (q < tot) {
+        v[u] = buf[c * cs + swz<E>(pos)];
+        if constexpr (SK == SK_RES) aux[u] = __ldg(P.slot + jj[u]);
+        if constexpr (SK == SK_H || SK == SK_ARG) aux[u] = bb ? (int)in_bits(bb, jj[u]) : 0;
+      }
+    }
+    E yv[kU];
+    if constexpr (SK == SK_RES) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) yv[u] = (q0 + u * kLT < tot && aux[u] >= 0) ? yb[aux[u]] : zero<E>();
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (q0 + u * kLT >= tot) continue;
+      const E o = scale(v[u], scl);
+      const int j = jj[u];
+      if constexpr (SK == SK_H || SK == SK_ARG) {
+        if (SK == SK_H && dst) dst[j] = o;
+        if (!aux[u]) {
+          const V a = norm2(o);
+          if (better(a, j, bv, bj)) {
+            bv = a;
+            bj = j;
+          }
+        }
+      } else if constexpr (SK == SK_RES) {
+        if (aux[u] >= 0) dst[j] = sub(yv[u], o);
+      } else {
+        dst[j] = o;
+      }
     }
   }
   if constexpr (SK == SK_H || SK == SK_ARG) {
@@ -382,6 +492,17 @@ __global__ void roots_kernel(int logN, int wsh, double2* lo64, double2* hi64, fl
 }
 
 // --------------------------------------------------------- least squares
+// The FP64 column append of step 6 (the update of cs_ls.cuh: u = B g,
+// d^2 = c(0) - ||u||^2, zeta = (h_0(lambda) - u^H z)/d, new row
+// w = -u^H B / d, x += zeta conj(w)) split over G CTAs per instance so that a
+// single large instance uses the whole GPU's FP64 units:
+//   lls_u_kernel  step 3 (every CTA reduces the arg-max partials the same
+//                 way), then u_i for a block of rows of B with equal area,
+//                 plus the CTA's share of ||u||^2 and u^H z;
+//   lls_w_kernel  every CTA adds the G shares in the same order, so all take
+//                 the same d, zeta and halting decision; then w_k and x_k for
+//                 a block of columns of equal area; the last CTA to finish
+//                 (a ticket counter, no waiting) applies step 8.
 template <class E>
 struct LOmpArgs {
   using W = typename FT<E>::W;
@@ -400,35 +521,28 @@ struct LOmpArgs {
   W* B;            // [batch][K(K+1)/2]
   W* z;            // [batch][K]
   W* x;            // [batch][K]
+  W* u;            // [batch][K]
   E* xw;           // [batch][K]
   int* lam;        // [batch][K]
   LState* st;      // [batch]
   V* part_v;       // [batch][nparts]
   int* part_j;
   int nparts;
+  double* ypart;   // [batch][nyp] shares of ||y||^2 from the first pass
+  int nyp;
+  double* terms;   // [batch][gmax][3] per-CTA shares of ||u||^2 and u^H z
+  int gmax;
 };
 
-template <class E>
-struct LLsLayout {
-  size_t g, part, terms, red, rv, rj, total;
-};
-
-template <class E>
-__host__ __device__ inline LLsLayout<E> lls_layout(int K) {
-  using W = typename FT<E>::W;
-  using V = typename NormT<E>::V;
-  LLsLayout<E> L;
-  const int Kc = K > 0 ? K : 1;
-  size_t o = 0;
-  L.g = o;     o = al16(o + (size_t)Kc * sizeof(W));
-  L.part = o;  o = al16(o + (size_t)(2 * kLT > Kc ? 2 * kLT : Kc) * sizeof(W));
-  L.terms = o; o = al16(o + (size_t)3 * Kc * sizeof(double));
-  L.red = o;   o = al16(o + 33 * sizeof(double));
-  L.rv = o;    o = al16(o + 34 * sizeof(V));
-  L.rj = o;    o = al16(o + 34 * sizeof(int));
-  L.total = o;
-  return L;
+// Boundaries of G blocks of equal area over p rows of a lower triangle
+// (row i has i + 1 entries): rows [row_cut(g), row_cut(g + 1)).  Columns
+// (column k has p - k entries) use the mirror image.
+__device__ __forceinline__ int row_cut(int p, int g, int G) {
+  if (g >= G) return p;
+  const int r = (int)((double)p * sqrt((double)g / (double)G) + 0.5);
+  return r < p ? r : p;
 }
+__device__ __forceinline__ int col_cut(int p, int g, int G) { return p - row_cut(p, G - g, G); }
 
 template <class E>
 __device__ void lwrite_outputs(const LOmpArgs<E>& a, int64_t b, int p, double ynorm2, double rn2) {
@@ -437,8 +551,8 @@ __device__ void lwrite_outputs(const LOmpArgs<E>& a, int64_t b, int p, double yn
   const W* xb = a.x + b * K;
   const int* lb = a.lam + b * K;
   for (int k = threadIdx.x; k < K; k += kLT) {
-    if (a.x_out) a.x_out[b * K + k] = k < p ? xb[k] : W{};
-    a.supp_out[b * K + k] = k < p ? lb[k] : -1;
+    if (a.x_out) a.x_out[b * K + k] = k < p ? __ldcg(xb + k) : W{};
+    a.supp_out[b * K + k] = k < p ? __ldcg(lb + k) : -1;
   }
   if (threadIdx.x == 0) {
     if (a.iters_out) a.iters_out[b] = p;
@@ -447,97 +561,199 @@ __device__ void lwrite_outputs(const LOmpArgs<E>& a, int64_t b, int p, double yn
   }
 }
 
-// One iteration's identification (reduction of the partials), least-squares
-// append and halting test for instance blockIdx.x.
+template <class V>
+__device__ __forceinline__ int reduce_partials(const V* pv, const int* pj, int n, V* rv, int* rj, V* sv, int* sj) {
+  V bv = (V)-1;
+  int bj = 0x7fffffff;
+  for (int i = threadIdx.x; i < n; i += kLT) {
+    const V v = pv[i];
+    const int j = pj[i];
+    if (v >= (V)0 && better(v, j, bv, bj)) {
+      bv = v;
+      bj = j;
+    }
+  }
+  block_partial(bv, bj, rv, rj, sv, sj);
+  __syncthreads();
+  return *sj;
+}
+
+// grid (G, batch); dynamic smem: K FP64 elements (the Gram column g)
 template <class E>
-__global__ void __launch_bounds__(kLT) lls_kernel(LOmpArgs<E> a, int nparts) {
+__global__ void __launch_bounds__(kLT) lls_u_kernel(LOmpArgs<E> a, int nparts) {
   using W = typename FT<E>::W;
   using V = typename NormT<E>::V;
+  constexpr bool DFT = FT<E>::C;
   extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ LsShared<W> sh;
-  __shared__ double rn2;
-  __shared__ V sel_v;
-  __shared__ int sel_j;
-  const int64_t b = blockIdx.x;
+  W* gk = (W*)sm;
+  __shared__ V rv[34], sv;
+  __shared__ int rj[34], sj;
+  __shared__ double red[kLT / 32];
+  const int64_t b = blockIdx.y;
+  const int G = gridDim.x, gi = blockIdx.x;
   LState* S = a.st + b;
   if (S->done) return;
-  const LLsLayout<E> L = lls_layout<E>(a.K);
-  const Grp g = whole_block();
-  const int N = a.P.N, M = a.P.M, K = a.K;
-  const int p = S->p;
+  const int N = a.P.N, K = a.K, p = S->p;
+  // step 3: the column with the largest |h(j)|^2
+  const int l = reduce_partials(a.part_v + b * a.nparts, a.part_j + b * a.nparts, nparts, rv, rj, &sv, &sj);
   double ynorm2 = S->ynorm2;
-  // step 3: the column with the largest |h(j)|^2 over all partials
-  {
-    V bv = (V)-1;
-    int bj = 0x7fffffff;
-    for (int i = threadIdx.x; i < nparts; i += kLT) {
-      const V v = a.part_v[b * a.nparts + i];
-      const int j = a.part_j[b * a.nparts + i];
-      if (v >= (V)0 && better(v, j, bv, bj)) {
-        bv = v;
-        bj = j;
-      }
-    }
-    block_partial(bv, bj, (V*)(sm + L.rv), (int*)(sm + L.rj), &sel_v, &sel_j);
-  }
-  if (p == 0) {  // t = 1: ||y||^2 in FP64
-    double yy[1] = {0.0};
-    const E* yb = a.y + b * M;
-    for (int m = threadIdx.x; m < M; m += kLT) yy[0] += norm2(to_w(yb[m]));
-    group_sum(g, yy, (double*)(sm + L.red));
-    ynorm2 = yy[0];
+  if (p == 0) {  // ||y||^2 from the first pass's shares, in a fixed order
+    double t = 0.0;
+    for (int i = threadIdx.x; i < a.nyp; i += kLT) t += a.ypart[b * a.nyp + i];
+    ynorm2 = block_sum0(t, red);
+    __syncthreads();
+    if (threadIdx.x == 0) red[0] = ynorm2;
+    __syncthreads();
+    ynorm2 = red[0];
     if (!(ynorm2 > 0.0) || K == 0) {  // zero measurement (or K = 0): no iteration
-      lwrite_outputs(a, b, 0, ynorm2, ynorm2);
+      if (gi == 0) lwrite_outputs(a, b, 0, ynorm2, ynorm2);
       return;
     }
-    if (threadIdx.x == 0) rn2 = ynorm2;
-  } else if (threadIdx.x == 0) {
-    rn2 = S->rn2;
+  }
+  if (l < 0) {  // no candidate column left
+    if (gi == 0) lwrite_outputs(a, b, p, ynorm2, p == 0 ? ynorm2 : S->rn2);
+    return;
+  }
+  if (gi == 0 && threadIdx.x == 0) {
+    S->pad1 = l;
+    if (p == 0) {
+      S->ynorm2 = ynorm2;
+      S->rn2 = ynorm2;
+    }
+  }
+  // u_i = sum_{k<=i} B[i][k] g_k for this CTA's rows; g_k = c(lambda_k (-) lambda)
+  const int r0 = row_cut(p, gi, G), r1 = row_cut(p, gi + 1, G);
+  const int* lam = a.lam + b * K;
+  for (int k = threadIdx.x; k < r1; k += kLT) {
+    const int d = DFT ? ((lam[k] - l) & (N - 1)) : (lam[k] ^ l);
+    gk[k] = a.P.c64[d];
   }
   __syncthreads();
-  const int l = sel_j;
-  if (l < 0) {  // no candidate column left
-    lwrite_outputs(a, b, p, ynorm2, rn2);
-    return;
+  const W* B = a.B + b * (((int64_t)K * (K + 1)) >> 1);
+  const W* z = a.z + b * K;
+  W* u = a.u + b * K;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double an = 0.0, ar = 0.0, ai = 0.0;
+  for (int i = r0 + w; i < r1; i += kLT / 32) {
+    const W* Bi = B + pidx(i);
+    W acc = W{};
+    for (int k = lane; k <= i; k += 32) acc = fmav(acc, Bi[k], gk[k]);
+    const double sr = warp_sum(re(acc));
+    const double si = DFT ? warp_sum(im(acc)) : 0.0;
+    if (lane == 0) {
+      const W ui = make_w<W>(sr, si);
+      u[i] = ui;
+      const W t = cmul(ui, z[i]);  // conj(u_i) z_i
+      an += norm2(ui);
+      ar += re(t);
+      ai += im(t);
+    }
   }
-  LsView<E> lv;
-  lv.B = a.B + b * (((int64_t)K * (K + 1)) >> 1);
-  lv.z = a.z + b * K;
-  lv.x = a.x + b * K;
-  lv.g = (W*)(sm + L.g);
-  lv.part = (W*)(sm + L.part);
-  lv.terms = (double*)(sm + L.terms);
-  lv.xw = a.xw + b * K;
-  lv.lam = a.lam + b * K;
-  lv.bits = a.bits + b * (int64_t)(N >> 5);
-  lv.kidx = nullptr;
-  PlanDev<E> pd;
-  pd.N = N;
-  pd.logN = a.P.logN;
-  pd.M = M;
-  pd.slot = a.P.slot;
-  pd.tw = nullptr;
-  pd.c = a.P.c;
-  pd.c64 = a.P.c64;
-  ls_append(g, pd, lv, a.h0 + b * (int64_t)N, p, l, rn2, sh);  // step 6
-  if (sh.st == 1) {                                            // column dependent on Lambda
-    lwrite_outputs(a, b, p, ynorm2, rn2);
-    return;
-  }
-  if (p + 1 >= K || rn2 < a.rel_tol * a.rel_tol * ynorm2) {  // step 8
-    lwrite_outputs(a, b, p + 1, ynorm2, rn2);
-    return;
-  }
-  if (a.xz) {  // zero-filled x for the next transform iteration
-    E* xzb = a.xz + b * (int64_t)N;
-    for (int k = threadIdx.x; k <= p; k += kLT) xzb[lv.lam[k]] = lv.xw[k];
-  }
+  // the CTA's shares, fixed order
+  double* tb = a.terms + (b * a.gmax + gi) * 3;
+  const double s0 = block_sum0(an, red);
+  __syncthreads();
+  const double s1 = block_sum0(ar, red);
+  __syncthreads();
+  const double s2 = block_sum0(ai, red);
   if (threadIdx.x == 0) {
-    S->p = p + 1;
-    S->ynorm2 = ynorm2;
-    S->rn2 = rn2;
+    tb[0] = s0;
+    tb[1] = s1;
+    tb[2] = s2;
   }
 }
+
+// grid (G, batch), same G as the lls_u_kernel launch before it
+template <class E>
+__global__ void __launch_bounds__(kLT) lls_w_kernel(LOmpArgs<E> a) {
+  using W = typename FT<E>::W;
+  __shared__ int ticket;
+  const int64_t b = blockIdx.y;
+  const int G = gridDim.x, gi = blockIdx.x;
+  LState* S = a.st + b;
+  if (S->done) return;
+  const int N = a.P.N, K = a.K, p = S->p, l = S->pad1;
+  const double ynorm2 = S->ynorm2;
+  double rn2 = S->rn2;
+  // every CTA adds the G shares in the same order: identical d and zeta
+  double an = 0.0, ar = 0.0, ai = 0.0;
+  for (int g = 0; g < G; ++g) {
+    const double* tb = a.terms + (b * a.gmax + g) * 3;
+    an += tb[0];
+    ar += tb[1];
+    ai += tb[2];
+  }
+  const double d2 = re(a.P.c64[0]) - an;
+  if (!(d2 > 1e-10 * ((double)a.P.M / (double)N))) {  // column dependent on Lambda: not added
+    if (gi == 0) lwrite_outputs(a, b, p, ynorm2, rn2);
+    return;
+  }
+  const double invd = rsqrt(d2);
+  const W bp = to_w(a.h0[b * (int64_t)N + l]);  // (Phi^H y)(lambda)
+  const W zeta = scale(sub(bp, make_w<W>(ar, ai)), invd);
+  rn2 -= norm2(zeta);
+  W* B = a.B + b * (((int64_t)K * (K + 1)) >> 1);
+  W* x = a.x + b * K;
+  E* xw = a.xw + b * K;
+  const W* u = a.u + b * K;
+  const int* lam = a.lam + b * K;
+  E* xz = a.xz ? a.xz + b * (int64_t)N : nullptr;
+  // w_k = -invd sum_{i=k}^{p-1} conj(u_i) B[i][k], one column per thread;
+  // a warp walks the rows in step from its first column so that its reads
+  // of row i are one contiguous segment
+  const int k0 = col_cut(p, gi, G), k1 = col_cut(p, gi + 1, G);
+  for (int kw = k0 + (threadIdx.x & ~31); kw < k1; kw += kLT) {
+    const int k = kw + (threadIdx.x & 31);
+    if (k >= k1) continue;
+    W acc = W{};
+    for (int i = kw; i < p; ++i)
+      if (i >= k) acc = fmacv(acc, u[i], B[pidx(i) + k]);
+    const W wk = scale(acc, -invd);
+    B[pidx(p) + k] = wk;
+    const W xk = fmacv(x[k], wk, zeta);
+    x[k] = xk;
+    const E e = from_w<E>(xk);
+    xw[k] = e;
+    if (xz) xz[lam[k]] = e;
+  }
+  if (gi == 0 && threadIdx.x == 0) {
+    B[pidx(p) + p] = make_w<W>(invd, 0.0);
+    a.z[b * K + p] = zeta;
+    const W xp = scale(zeta, invd);
+    x[p] = xp;
+    const E e = from_w<E>(xp);
+    xw[p] = e;
+    if (xz) xz[l] = e;
+    a.lam[b * K + p] = l;
+    a.bits[b * (int64_t)(N >> 5) + (l >> 5)] |= 1u << (l & 31);
+  }
+  // the last CTA of this instance to get here applies step 8
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    ticket = atomicAdd(&S->pad0, 1);
+  }
+  __syncthreads();
+  if (ticket != G - 1) return;
+  __threadfence();
+  if (p + 1 >= K || rn2 < a.rel_tol * a.rel_tol * ynorm2) {
+    lwrite_outputs(a, b, p + 1, ynorm2, rn2);
+  } else if (threadIdx.x == 0) {
+    S->p = p + 1;
+    S->rn2 = rn2;
+  }
+  if (threadIdx.x == 0) S->pad0 = 0;
+}
+
+// CTAs per instance for the least squares at p columns: about 8192 complex
+// FP64 multiply-adds each, at most gmax
+inline int ls_ctas(int p, int gmax) {
+  const int64_t work = (int64_t)p * (p + 1) / 2;
+  int64_t g = (work + 8191) / 8192;
+  if (g < 1) g = 1;
+  return (int)(g < gmax ? g : gmax);
+}
+
 
 // ------------------------------------------------------------- launchers
 template <class K>
@@ -547,25 +763,25 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 template <class E, bool DFT, int LD>
-cudaError_t run_col(const LDev<E>& P, const E* in, int64_t in_stride, int conj_in, E* out, const LState* st,
-                    int64_t batch, cudaStream_t s) {
-  const size_t smem = pass_smem<E>(1 << P.n1);
+cudaError_t run_col(const LDev<E>& P, const E* in, int64_t in_stride, E* out, const LState* st, int64_t batch,
+                    cudaStream_t s, double* ynorm = nullptr) {
+  const size_t smem = pass_layout<E>(1 << P.n1).total;
   cudaError_t e = allow_smem(lcol_kernel<E, DFT, LD>, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((1u << P.n2) / tile_c<E>(), (unsigned)batch);
-  lcol_kernel<E, DFT, LD><<<grid, kLT, smem, s>>>(P, in, in_stride, conj_in, out, st);
+  lcol_kernel<E, DFT, LD><<<grid, kLT, smem, s>>>(P, in, in_stride, out, st, ynorm);
   return cudaGetLastError();
 }
 
 template <class E, bool DFT, int SK>
-cudaError_t run_row(const LDev<E>& P, const E* T, int conj_out, double scl, E* out, const E* y,
-                    const uint32_t* bits, typename NormT<E>::V* pv, int* pj, int nparts, const LState* st,
-                    int64_t batch, cudaStream_t s) {
-  const size_t smem = pass_smem<E>(1 << P.n2);
+cudaError_t run_row(const LDev<E>& P, const E* T, int neg, double scl, E* out, const E* y, const uint32_t* bits,
+                    typename NormT<E>::V* pv, int* pj, int nparts, const LState* st, int64_t batch,
+                    cudaStream_t s) {
+  const size_t smem = pass_layout<E>(1 << P.n2).total;
   cudaError_t e = allow_smem(lrow_kernel<E, DFT, SK>, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((1u << P.n1) / tile_c<E>(), (unsigned)batch);
-  lrow_kernel<E, DFT, SK><<<grid, kLT, smem, s>>>(P, T, conj_out, (typename FT<E>::R)scl, out, y, bits, pv, pj,
+  lrow_kernel<E, DFT, SK><<<grid, kLT, smem, s>>>(P, T, neg, (typename FT<E>::R)scl, out, y, bits, pv, pj,
                                                   nparts, st);
   return cudaGetLastError();
 }
@@ -612,7 +828,7 @@ cudaError_t corr_t(const PlanView& Pv, const void* r, int64_t batch, void* h, in
   E* T = (E*)w;
   V* pv = (V*)(w + al16((size_t)batch * P.N * sizeof(E)));
   int* pj = (int*)((unsigned char*)pv + al16((size_t)batch * np * sizeof(V)));
-  cudaError_t e = run_col<E, DFT, LD_ZF>(P, (const E*)r, P.M, DFT, T, nullptr, batch, s);
+  cudaError_t e = run_col<E, DFT, LD_ZF>(P, (const E*)r, P.M, T, nullptr, batch, s);
   if (e != cudaSuccess) return e;
   e = run_row<E, DFT, SK_H>(P, T, DFT, inv_sqrt_n(P.logN), (E*)h, nullptr, nullptr, amax ? pv : nullptr,
                             amax ? pj : nullptr, np, nullptr, batch, s);
@@ -657,8 +873,8 @@ cudaError_t fast_t(const PlanView& Pv, const void* h0, const int32_t* supp, cons
 // ------------------------------------------------------------------- OMP
 template <class E>
 struct LOmpWs {
-  size_t st, h0, T, Z, xz, bits, B, z, x, xw, lam, pv, pj, total;
-  int nparts;
+  size_t st, h0, T, Z, xz, bits, B, z, x, u, xw, lam, pv, pj, yp, tm, total;
+  int nparts, nyp, gmax;
 };
 
 template <class E>
@@ -682,10 +898,18 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
   L.B = o;    o = al16(o + (size_t)batch * ((Kc * (Kc + 1)) / 2) * sizeof(W));
   L.z = o;    o = al16(o + (size_t)batch * Kc * sizeof(W));
   L.x = o;    o = al16(o + (size_t)batch * Kc * sizeof(W));
+  L.u = o;    o = al16(o + (size_t)batch * Kc * sizeof(W));
   L.xw = o;   o = al16(o + (size_t)batch * Kc * sizeof(E));
   L.lam = o;  o = al16(o + (size_t)batch * Kc * sizeof(int));
   L.pv = o;   o = al16(o + (size_t)batch * L.nparts * sizeof(V));
   L.pj = o;   o = al16(o + (size_t)batch * L.nparts * sizeof(int));
+  L.nyp = (1 << P.n2) / tile_c<E>();
+  L.yp = o;   o = al16(o + (size_t)batch * L.nyp * sizeof(double));
+  {  // CTAs per instance for the least squares: fill about 4 waves of the GPU
+    int64_t g = (4 * 152 + batch - 1) / batch;
+    L.gmax = (int)(g < 1 ? 1 : (g > 256 ? 256 : g));
+  }
+  L.tm = o;   o = al16(o + (size_t)batch * L.gmax * 3 * sizeof(double));
   L.total = o;
   return L;
 }
@@ -719,24 +943,28 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
   A.x = (W*)(w + L.x);
   A.xw = (E*)(w + L.xw);
   A.lam = (int*)(w + L.lam);
+  A.u = (W*)(w + L.u);
   A.part_v = (V*)(w + L.pv);
   A.part_j = (int*)(w + L.pj);
   A.nparts = L.nparts;
+  A.ypart = (double*)(w + L.yp);
+  A.nyp = L.nyp;
+  A.terms = (double*)(w + L.tm);
+  A.gmax = L.gmax;
   const size_t Nv = (size_t)batch * P.N * sizeof(E);
   cudaError_t e;
   if ((e = cudaMemsetAsync(A.st, 0, (size_t)batch * sizeof(LState), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(A.bits, 0, (size_t)batch * (P.N >> 5) * sizeof(uint32_t), s)) != cudaSuccess) return e;
   if (Z && (e = cudaMemsetAsync(Z, 0, Nv, s)) != cudaSuccess) return e;
   if (A.xz && (e = cudaMemsetAsync(A.xz, 0, Nv, s)) != cudaSuccess) return e;
-  const size_t ls_smem = lls_layout<E>(a.K).total;
-  if ((e = allow_smem(lls_kernel<E>, ls_smem)) != cudaSuccess) return e;
+  const size_t ls_smem = (size_t)(a.K > 0 ? a.K : 1) * sizeof(W);
   const double isq = inv_sqrt_n(P.logN);
   const int rp = row_parts(P), fp = fast_parts(P);
   const int T_end = a.K > 0 ? a.K : 1;
   for (int t = 1; t <= T_end; ++t) {
     int np;
     if (t == 1) {  // h_0 = Phi^H y by one transform (Eq. kernelsumOMP, first case)
-      if ((e = run_col<E, DFT, LD_ZF>(P, A.y, P.M, DFT, T, A.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_col<E, DFT, LD_ZF>(P, A.y, P.M, T, A.st, batch, s, A.ypart)) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_H>(P, T, DFT, isq, A.h0, nullptr, nullptr, A.part_v, A.part_j, L.nparts, A.st,
                                      batch, s)) != cudaSuccess)
         return e;
@@ -747,17 +975,20 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
         return e;
       np = fp;
     } else {  // r = y - Phi x by a forward transform of zf(x), then h = A^H zf(r)
-      if ((e = run_col<E, DFT, LD_DENSE>(P, A.xz, P.N, 0, T, A.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_col<E, DFT, LD_DENSE>(P, A.xz, P.N, T, A.st, batch, s)) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s)) !=
           cudaSuccess)
         return e;
-      if ((e = run_col<E, DFT, LD_DENSE>(P, Z, P.N, DFT, T, A.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_col<E, DFT, LD_DENSE>(P, Z, P.N, T, A.st, batch, s)) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_ARG>(P, T, DFT, isq, nullptr, nullptr, A.bits, A.part_v, A.part_j, L.nparts,
                                        A.st, batch, s)) != cudaSuccess)
         return e;
       np = rp;
     }
-    lls_kernel<E><<<(unsigned)batch, kLT, ls_smem, s>>>(A, np);
+    const dim3 lg((unsigned)ls_ctas(t - 1, L.gmax), (unsigned)batch);
+    lls_u_kernel<E><<<lg, kLT, ls_smem, s>>>(A, np);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    lls_w_kernel<E><<<lg, kLT, 0, s>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -767,7 +998,7 @@ template <class W>
 cudaError_t kv_t(const PlanView& Pv, void* c64, void* tmp, cudaStream_t s) {
   constexpr bool DFT = FT<W>::C;
   const LDev<W> P = ldev<W>(Pv);
-  cudaError_t e = run_col<W, DFT, LD_ONES>(P, nullptr, 0, 0, (W*)tmp, nullptr, 1, s);
+  cudaError_t e = run_col<W, DFT, LD_ONES>(P, nullptr, 0, (W*)tmp, nullptr, 1, s);
   if (e != cudaSuccess) return e;
   // c = N^{-1} A^H 1_Omega scaled as in Eq. (kernelsum): N^{-1} F^H zf(1)
   return run_row<W, DFT, SK_KV>(P, (const W*)tmp, DFT, std::ldexp(1.0, -P.logN), (W*)c64, nullptr, nullptr,
