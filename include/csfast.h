@@ -210,6 +210,75 @@ cs_status cs_plan_tune(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t
                        int32_t* t_best, int32_t* cand_out, float* ms_out, int32_t cap, int32_t* n_out,
                        void* stream);
 
+/* ---------------------------------------------------------------- serving
+ * A request runtime for recovery jobs of mixed N, M, K, kind, precision and
+ * algorithm (the paper has no counterpart: this is the serving side of the
+ * same path).  `workers` threads each own a CUDA stream on the device that
+ * is current at cs_server_create.  A submitted job waits in a queue until a
+ * worker is free and its device footprint (its plan's tables, workspace,
+ * input and outputs) fits in what the memory budget has left; the worker
+ * then builds the job's plan on its stream, runs the solve, copies the
+ * results to the caller's host buffers and releases the job's memory, all
+ * stream-ordered, so jobs of different workers overlap on the GPU and no
+ * admission or release synchronises the device.  Admission is oldest first,
+ * except that a later job that fits may start while the oldest does not fit;
+ * once the oldest has been passed 8 times, nothing else starts before it.
+ * Results are the same as a single cs_omp / cs_cosamp / cs_sp call on the
+ * job alone. */
+typedef enum { CS_ALGO_OMP = 0, CS_ALGO_COSAMP = 1, CS_ALGO_SP = 2 } cs_algo;
+
+typedef struct {
+  int32_t kind, prec, algo, K;
+  int64_t N, M;
+  const int32_t* omega_host;  /* [M], sorted; copied by cs_server_submit */
+  const void* y_host;         /* [M] in the plan's element type; copied by cs_server_submit */
+  cs_halt halt;
+} cs_request;
+
+typedef struct {
+  int64_t ticket;
+  int32_t status;        /* cs_status of the job's solve */
+  int32_t iters;         /* as cs_omp's iters_dev (cs_sp / cs_cosamp: iterations) */
+  int32_t device_error;  /* cs_plan_status of the job's plan after the solve */
+  int32_t pad;
+  double resnorm;        /* as cs_omp's resnorm_dev */
+  double t_submit_us, t_admit_us, t_done_us;  /* host clock, microseconds since cs_server_create */
+  int64_t footprint_bytes;
+} cs_result;
+
+typedef struct cs_server_s* cs_server_t;
+
+/* Start `workers` (1..64) worker threads with a device-memory budget of
+ * hbm_budget_bytes for the jobs in flight. */
+cs_status cs_server_create(int32_t workers, int64_t hbm_budget_bytes, cs_server_t* out);
+
+/* Queue one job; returns at once with its ticket.  The request is checked
+ * as cs_plan_create and the solve call would check it (CS_ERR_INVALID /
+ * CS_ERR_UNSUPPORTED, synchronously); a job whose footprint exceeds the
+ * whole budget is refused with CS_ERR_NOMEM.  omega and y are copied; x_host
+ * (FP64 [K], complex interleaved for DFT) and supp_host (int32 [K]) receive
+ * the results and must stay valid until the job's result has been polled. */
+cs_status cs_server_submit(cs_server_t server, const cs_request* req, void* x_host, int32_t* supp_host,
+                           int64_t* ticket);
+
+/* Move up to `max` finished jobs' results to out (oldest finished first),
+ * waiting up to wait_ms for the first one if none is ready; *n = count. */
+cs_status cs_server_poll(cs_server_t server, cs_result* out, int32_t max, int32_t wait_ms, int32_t* n);
+
+/* Jobs waiting, running and finished so far, and the budget in use. */
+cs_status cs_server_stats(cs_server_t server, int64_t* pending, int64_t* running, int64_t* completed,
+                          int64_t* bytes_in_use);
+
+/* Finish every queued job, stop the workers and free the server (results
+ * not polled yet are dropped). */
+cs_status cs_server_destroy(cs_server_t server);
+
+/* The admission rule on its own (host only, no device): given the pending
+ * jobs' footprints oldest first and how often each has been passed, the
+ * budget in use and the budget, the index of the job to start now, or -1. */
+int32_t cs_admit_next(const int64_t* footprints, const int32_t* bypassed, int32_t n_pending, int64_t in_use,
+                      int64_t budget, int32_t max_bypass);
+
 /* Short static description of a status code. */
 const char* cs_status_string(cs_status s);
 

@@ -24,7 +24,8 @@ PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 # Every function include/csfast.h declares.
 EXPORTS = ["cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
            "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
-           "cs_status_string", "cs_last_error"]
+           "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy",
+           "cs_admit_next", "cs_status_string", "cs_last_error"]
 
 
 class CsError(RuntimeError):
@@ -34,6 +35,22 @@ class CsError(RuntimeError):
 class Halt(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("path", ctypes.c_int32), ("t_switch", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("algo", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("N", ctypes.c_int64), ("M", ctypes.c_int64), ("omega_host", ctypes.POINTER(ctypes.c_int32)),
+                ("y_host", ctypes.c_void_p), ("halt", Halt)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("device_error", ctypes.c_int32), ("pad", ctypes.c_int32), ("resnorm", ctypes.c_double),
+                ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_int64)]
+
+
+ALGOS = {"omp": 0, "cosamp": 1, "sp": 2}
 
 
 _lib = None
@@ -63,8 +80,16 @@ def load(path: str = LIB_PATH):
     L.cs_cosamp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_plan_tune.argtypes = [vp, vp, i64, i32, ctypes.c_double, pi32, pi32, ctypes.POINTER(ctypes.c_float), i32,
                                pi32, vp]
+    L.cs_server_create.argtypes = [i32, i64, ctypes.POINTER(vp)]
+    L.cs_server_submit.argtypes = [vp, ctypes.POINTER(Request), vp, pi32, pi64]
+    L.cs_server_poll.argtypes = [vp, ctypes.POINTER(Result), i32, i32, pi32]
+    L.cs_server_stats.argtypes = [vp, pi64, pi64, pi64, pi64]
+    L.cs_server_destroy.argtypes = [vp]
+    L.cs_admit_next.argtypes = [pi64, pi32, i32, i64, i64, i32]
+    L.cs_admit_next.restype = ctypes.c_int32
     for f in ("cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
-              "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune"):
+              "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
+              "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy"):
         getattr(L, f).restype = ctypes.c_int
     L.cs_status_string.argtypes = [ctypes.c_int]
     L.cs_status_string.restype = ctypes.c_char_p
@@ -224,3 +249,76 @@ class Plan:
         res = torch.empty(B, dtype=torch.float64, device="cuda")
         self.pursuit_into(algo, y, K, x, supp, iters, res, rel_tol, path, max_iter, stream=stream)
         return x, supp, iters, res
+
+
+def admit_next(footprints, bypassed, in_use: int, budget: int, max_bypass: int = 8) -> int:
+    """cs_admit_next: the runtime's admission rule (host only)."""
+    n = len(footprints)
+    fp = (ctypes.c_int64 * max(n, 1))(*footprints)
+    by = (ctypes.c_int32 * max(n, 1))(*bypassed)
+    return int(load().cs_admit_next(fp, by, n, in_use, budget, max_bypass))
+
+
+class Server:
+    """The request runtime (cs_server_*): jobs of mixed sizes, kinds and
+    algorithms admitted under a device-memory budget onto `workers` streams."""
+
+    def __init__(self, workers: int = 4, budget_bytes: int = 8 << 30):
+        h = ctypes.c_void_p()
+        _check(load().cs_server_create(workers, int(budget_bytes), ctypes.byref(h)))
+        self._h = h
+        self._jobs = {}
+
+    def submit(self, kind: str, prec: str, N: int, omega, y, K: int, algo: str = "omp", rel_tol: float = 1e-6,
+               path: str = "hybrid", t_switch: int = -1, max_iter: int = 0) -> int:
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.int32))
+        dt = {"dft": {"fp32": np.complex64, "fp64": np.complex128}, "wht": {"fp32": np.float32, "fp64": np.float64}}
+        yv = np.ascontiguousarray(np.asarray(y, dtype=dt[kind][prec]))
+        x = np.zeros(max(K, 1), dtype=np.complex128 if kind == "dft" else np.float64)
+        supp = np.zeros(max(K, 1), dtype=np.int32)
+        req = Request(KINDS[kind], PRECS[prec], ALGOS[algo], K, int(N), int(om.size),
+                      om.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), yv.ctypes.data,
+                      Halt(rel_tol, PATHS[path], t_switch, max_iter))
+        t = ctypes.c_int64()
+        _check(load().cs_server_submit(self._h, ctypes.byref(req), x.ctypes.data,
+                                       supp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(t)))
+        self._jobs[t.value] = (x, supp, K)
+        return t.value
+
+    def poll(self, wait_ms: int = 0, max_results: int = 256) -> list:
+        buf = (Result * max_results)()
+        n = ctypes.c_int32()
+        _check(load().cs_server_poll(self._h, buf, max_results, wait_ms, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            x, supp, K = self._jobs.pop(r.ticket)
+            out.append({"ticket": r.ticket, "status": r.status, "iters": r.iters, "device_error": r.device_error,
+                        "resnorm": r.resnorm, "x": x[:K], "supp": supp[:K], "t_submit_us": r.t_submit_us,
+                        "t_admit_us": r.t_admit_us, "t_done_us": r.t_done_us, "footprint_bytes": r.footprint_bytes})
+        return out
+
+    def wait_all(self, timeout_s: float = 600.0) -> list:
+        import time
+        out, t0 = [], time.time()
+        while self._jobs and time.time() - t0 < timeout_s:
+            out += self.poll(wait_ms=100)
+        if self._jobs:
+            raise CsError(f"{len(self._jobs)} jobs not finished after {timeout_s} s")
+        return out
+
+    def stats(self) -> dict:
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(load().cs_server_stats(self._h, *[ctypes.byref(a) for a in v]))
+        return dict(zip(("pending", "running", "completed", "bytes_in_use"), (a.value for a in v)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().cs_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -28,6 +28,8 @@ struct cs_plan_s {
   int* d_status = nullptr;  // kernel-detected errors (cs_plan_status)
   void* ws = nullptr;       // OMP workspace (grows on demand, stream-ordered)
   size_t ws_bytes = 0;
+  bool ordered = false;     // every buffer stream-ordered on `home` (request runtime)
+  cudaStream_t home = nullptr;
 };
 
 static thread_local char g_err[256] = "";
@@ -71,16 +73,19 @@ static int plan_switch(const cs_plan_s* p) { return p->t_switch_tuned >= 0 ? p->
 
 static void plan_free(cs_plan_s* p) {
   if (!p) return;
-  cudaFree(p->d_slot);
-  cudaFree(p->d_tw64);
-  cudaFree(p->d_tw32);
-  cudaFree(p->d_c64);
-  cudaFree(p->d_c32);
-  cudaFree(p->d_lt64);
-  cudaFree(p->d_lt32);
-  cudaFree(p->d_status);
-  cudaFree(p->ws);
+  void* bufs[] = {p->d_slot, p->d_tw64, p->d_tw32, p->d_c64, p->d_c32, p->d_lt64, p->d_lt32, p->d_status, p->ws};
+  for (void* b : bufs) {
+    if (!b) continue;
+    if (p->ordered) cudaFreeAsync(b, p->home);
+    else cudaFree(b);
+  }
   delete p;
+}
+
+// Device allocation for a plan: plain, or stream-ordered on its home stream
+// (no device-wide synchronisation when it is released).
+static cudaError_t plan_alloc(cs_plan_s* p, void** ptr, size_t bytes) {
+  return p->ordered ? cudaMallocAsync(ptr, bytes, p->home) : cudaMalloc(ptr, bytes);
 }
 
 // Grows the plan's workspace to `need` bytes (stream-ordered).
@@ -94,8 +99,8 @@ static cs_status ensure_ws(cs_plan_s* plan, size_t need, cudaStream_t st) {
   return CS_OK;
 }
 
-extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
-                                    void* stream, cs_plan_t* out) {
+static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
+                                  void* stream, bool ordered, cs_plan_t* out) {
   if (!out) return CS_ERR_INVALID;
   *out = nullptr;
   if (kind != CS_WHT && kind != CS_DFT) return CS_ERR_INVALID;
@@ -115,6 +120,8 @@ extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_
   cs_plan_s* p = new (std::nothrow) cs_plan_s();
   if (!p) return CS_ERR_NOMEM;
   cudaStream_t st = (cudaStream_t)stream;
+  p->ordered = ordered;
+  p->home = st;
   p->kind = kind;
   p->prec = prec;
   cudaGetDevice(&p->device);
@@ -149,22 +156,22 @@ extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_
       return s_;                                \
     }                                           \
   } while (0)
-  PLAN_TRY(cudaMalloc(&p->d_slot, (size_t)N * sizeof(int32_t)), "cudaMalloc slot");
+  PLAN_TRY(plan_alloc(p, (void**)&p->d_slot, (size_t)N * sizeof(int32_t)), "cudaMalloc slot");
   PLAN_TRY(cudaMemcpyAsync(p->d_slot, slot.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, st),
            "copy slot");
   if (kind == CS_DFT && !large) {
-    PLAN_TRY(cudaMalloc(&p->d_tw64, (size_t)N * sizeof(double2)), "cudaMalloc twiddles");
-    if (prec == CS_FP32) PLAN_TRY(cudaMalloc(&p->d_tw32, (size_t)N * sizeof(float2)), "cudaMalloc twiddles");
+    PLAN_TRY(plan_alloc(p, &p->d_tw64, (size_t)N * sizeof(double2)), "cudaMalloc twiddles");
+    if (prec == CS_FP32) PLAN_TRY(plan_alloc(p, &p->d_tw32, (size_t)N * sizeof(float2)), "cudaMalloc twiddles");
   }
   if (kind == CS_DFT && large) {
     const size_t nt = ((size_t)1 << p->v.n1) + ((size_t)1 << p->v.n2) + ((size_t)1 << p->v.wsh) +
                       ((size_t)N >> p->v.wsh);
-    PLAN_TRY(cudaMalloc(&p->d_lt64, nt * sizeof(double2)), "cudaMalloc four-step tables");
-    if (prec == CS_FP32) PLAN_TRY(cudaMalloc(&p->d_lt32, nt * sizeof(float2)), "cudaMalloc four-step tables");
+    PLAN_TRY(plan_alloc(p, &p->d_lt64, nt * sizeof(double2)), "cudaMalloc four-step tables");
+    if (prec == CS_FP32) PLAN_TRY(plan_alloc(p, &p->d_lt32, nt * sizeof(float2)), "cudaMalloc four-step tables");
   }
-  PLAN_TRY(cudaMalloc(&p->d_c64, (size_t)N * wb), "cudaMalloc c");
-  if (prec == CS_FP32) PLAN_TRY(cudaMalloc(&p->d_c32, (size_t)N * wb / 2), "cudaMalloc c");
-  PLAN_TRY(cudaMalloc(&p->d_status, sizeof(int)), "cudaMalloc status");
+  PLAN_TRY(plan_alloc(p, &p->d_c64, (size_t)N * wb), "cudaMalloc c");
+  if (prec == CS_FP32) PLAN_TRY(plan_alloc(p, &p->d_c32, (size_t)N * wb / 2), "cudaMalloc c");
+  PLAN_TRY(plan_alloc(p, (void**)&p->d_status, sizeof(int)), "cudaMalloc status");
   PLAN_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st), "clear status");
   p->v.slot = p->d_slot;
   p->v.tw64 = p->d_tw64;
@@ -181,10 +188,11 @@ extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_
   } else {
     void* tmp = nullptr;
     PLAN_TRY(large_tables(p->v, p->d_lt64, p->d_lt32, st), "four-step tables");
-    PLAN_TRY(cudaMalloc(&tmp, (size_t)N * wb), "cudaMalloc plan scratch");
+    PLAN_TRY(plan_alloc(p, &tmp, (size_t)N * wb), "cudaMalloc plan scratch");
     e = large_kernel_vector(p->v, p->d_c64, p->d_c32, tmp, st);
+    if (ordered) cudaFreeAsync(tmp, st);
     const cudaError_t e2 = cudaStreamSynchronize(st);
-    cudaFree(tmp);
+    if (!ordered) cudaFree(tmp);
     PLAN_TRY(e, "kernel-vector kernels");
     PLAN_TRY(e2, "plan synchronize");
   }
@@ -192,6 +200,52 @@ extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_
   *out = p;
   return CS_OK;
 }
+
+extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
+                                    void* stream, cs_plan_t* out) {
+  return plan_create_impl(N, omega_host, M, kind, prec, stream, false, out);
+}
+
+namespace csf {
+// Plans of the request runtime: every buffer stream-ordered on `stream`, so
+// that creating and releasing one never synchronises the device.
+cs_status plan_create_ordered(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
+                              cudaStream_t stream, cs_plan_t* out) {
+  return plan_create_impl(N, omega_host, M, kind, prec, stream, true, out);
+}
+// Queues the release of a stream-ordered plan's buffers on its stream.
+void plan_release_ordered(cs_plan_t plan) { plan_free(plan); }
+
+// Device bytes a plan and one solve of `K` columns on one measurement take
+// (plan tables, the largest workspace of the path, inputs and outputs), for
+// admission against a memory budget.  algo: 0 OMP, 1 CoSaMP, 2 SP.
+size_t solve_footprint(int64_t N, int64_t M, int32_t kind, int32_t prec, int32_t K, int32_t algo) {
+  int logN = 0;
+  while ((int64_t(1) << logN) < N) ++logN;
+  PlanView v{};
+  v.N = (int)N;
+  v.logN = logN;
+  v.M = (int)M;
+  v.dft = kind == CS_DFT;
+  v.fp32 = prec == CS_FP32;
+  v.large = logN > kMaxLogN;
+  v.n1 = v.large ? logN / 2 : 0;
+  v.n2 = v.large ? logN - logN / 2 : 0;
+  v.wsh = v.large ? (logN + 1) / 2 : 0;
+  const size_t wb = v.dft ? 16 : 8, eb = elem_bytes(kind, prec);
+  size_t b = (size_t)N * 4 + (size_t)N * wb + (v.fp32 ? (size_t)N * wb / 2 : 0) + 256;
+  if (v.dft && !v.large) b += (size_t)N * (16 + (v.fp32 ? 8 : 0));
+  if (v.dft && v.large)
+    b += (((size_t)1 << v.n1) + ((size_t)1 << v.n2) + ((size_t)1 << v.wsh) + ((size_t)N >> v.wsh)) *
+         (16 + (v.fp32 ? 8 : 0));
+  if (v.large) b += (size_t)N * wb;  // kernel-vector scratch while the plan is built
+  size_t ws = 0;
+  if (algo == 0) ws = v.large ? large_omp_ws(v, K, CS_PATH_HYBRID, 1) : omp_workspace_bytes(v, K, 1);
+  else ws = pursuit_workspace_bytes(v, K, algo == 2 ? 0 : 1, 1);
+  b += ws + (size_t)M * eb + (size_t)K * (wb + 4) + 64;
+  return b;
+}
+}  // namespace csf
 
 extern "C" cs_status cs_plan_destroy(cs_plan_t plan) {
   if (!plan) return CS_ERR_INVALID;
