@@ -222,7 +222,51 @@ def secondary(args, dev, plan, inst, stream, flush):
                                   "fast_over_conv": per_it["fast"] / per_it["conv"],
                                   "paper_flop_model": costmodel.cosamp_fast_ratio(8192, 4)}
     out["large_dft_c64_N4194304_M524288"] = large_single(dev, stream, flush)
+    out["serving"] = serving(args.serve_requests)
     return out
+
+
+def _serving_gen(req):
+    return synth.serving_instance(req)
+
+
+def serving(n_req: int, rate: float = 2000.0, workers: int = 8, budget_gb: float = 64.0):
+    """The serving workload: Poisson arrivals at 2000 requests/s, N = 2^14 ..
+    2^20, M = N/8, K = 32 .. 1024, partial WHT or DFT by a coin, FP32, OMP
+    (hybrid switch), each request with its own Omega, replayed in real time
+    into the request runtime (cs_server_*) with `workers` streams and a
+    device-memory budget; latency = completion - arrival."""
+    from paper_1205_4139_gb300 import binding
+    reqs = synth.serving_requests(n_req, rate=rate, seed=0)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 1)) as pool:
+        data = pool.map(_serving_gen, reqs)
+    srv = binding.Server(workers=workers, budget_bytes=int(budget_gb * (1 << 30)))
+    # warm-up: one small job per kind through every path the stream uses
+    for kind in ("wht", "dft"):
+        w = synth.serving_requests(1, seed=99, log_n_lo=14, log_n_hi=14, k_lo=32, k_hi=32)[0]
+        w["kind"] = kind
+        om, yv = synth.serving_instance(w)
+        srv.submit(kind, "fp32", w["N"], om, yv, w["K"])
+    srv.wait_all()
+    t0 = time.perf_counter()
+    for r, (om, yv) in zip(reqs, data):
+        dt = r["arrival_s"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        srv.submit(r["kind"], "fp32", r["N"], om, yv, r["K"])
+    res = srv.wait_all()
+    srv.close()
+    bad = [r for r in res if r["status"] != 0 or r["device_error"] != 0]
+    lat = sorted((r["t_done_us"] - r["t_submit_us"]) * 1e-3 for r in res)
+    wait = sorted((r["t_admit_us"] - r["t_submit_us"]) * 1e-3 for r in res)
+    span = (max(r["t_done_us"] for r in res) - min(r["t_submit_us"] for r in res)) * 1e-6
+    q = lambda v, f: v[min(len(v) - 1, int(f * (len(v) - 1) + 0.5))]
+    return {"workload": f"{n_req} requests, Poisson {rate:g}/s, N=2^14..2^20, M=N/8, K=32..1024, WHT/DFT fp32, OMP",
+            "workers": workers, "budget_gb": budget_gb, "requests": len(res), "failed": len(bad),
+            "solves_per_s": len(res) / span, "latency_ms_p50": q(lat, 0.5), "latency_ms_p99": q(lat, 0.99),
+            "queue_wait_ms_p50": q(wait, 0.5), "makespan_s": span,
+            "offered_s": reqs[-1]["arrival_s"]}
 
 
 def large_single(dev, stream, flush, N=1 << 22, M=1 << 19, K=256):
@@ -395,6 +439,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle instances (default one per core)")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -119,3 +119,27 @@ def make_batch(kind: str, N: int, M: int, K: int, B: int, *, snr_db=None, dist="
 # Workloads used by the tests and the benchmark (sizes, not data).
 CONFIG_WHT_FP64_SINGLE = dict(kind=WHT, N=1024, M=256, K=16, B=1, snr_db=None, prec="fp64", seed=0)
 CONFIG_DFT_C64_BATCH = dict(kind=DFT, N=4096, M=1024, K=64, B=1024, snr_db=40.0, prec="fp32", seed=0)
+
+
+# Request stream of the serving workload: Poisson arrivals at `rate` per
+# second; N = 2^e with e uniform over [log_n_lo, log_n_hi]; M = N / 8; K
+# uniform over [k_lo, k_hi]; kind by a fair coin; noiseless Gaussian
+# nonzeros; each request has its own Omega and seed.
+def serving_requests(n: int, rate: float = 2000.0, seed: int = 0, log_n_lo: int = 14, log_n_hi: int = 20,
+                     k_lo: int = 32, k_hi: int = 1024) -> list[dict]:
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    out = []
+    for i in range(n):
+        N = 1 << int(rng.integers(log_n_lo, log_n_hi + 1))
+        M = N // 8
+        K = int(min(rng.integers(k_lo, k_hi + 1), M))
+        kind = DFT if rng.integers(0, 2) else WHT
+        out.append({"arrival_s": float(t[i]), "kind": kind, "N": N, "M": M, "K": K, "seed": seed * 100003 + i + 1})
+    return out
+
+
+def serving_instance(req: dict, prec: str = "fp32") -> tuple[np.ndarray, np.ndarray]:
+    """(Omega, y) of one serving request (one instance, noiseless)."""
+    inst = make_batch(req["kind"], req["N"], req["M"], req["K"], 1, snr_db=None, prec=prec, seed=req["seed"])
+    return inst["omega"], inst["Y"][0]

@@ -58,3 +58,17 @@ def test_simulated_queue_never_starves_the_large_job():
             break
     assert 90 in started[:9 + 1]
     assert not pending
+
+
+def test_serving_request_stream_shape():
+    import numpy as np
+    import synth
+    reqs = synth.serving_requests(400, rate=2000.0, seed=3)
+    t = np.array([r["arrival_s"] for r in reqs])
+    assert np.all(np.diff(t) > 0)
+    assert abs(np.mean(np.diff(t)) - 1 / 2000.0) < 0.2 / 2000.0  # Poisson at 2000/s
+    for r in reqs:
+        assert 1 << 14 <= r["N"] <= 1 << 20 and r["N"] & (r["N"] - 1) == 0
+        assert r["M"] == r["N"] // 8 and 32 <= r["K"] <= 1024 and r["kind"] in ("wht", "dft")
+    assert {r["N"] for r in reqs} == {1 << e for e in range(14, 21)}
+    assert len({r["seed"] for r in reqs}) == len(reqs)
