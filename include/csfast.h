@@ -249,7 +249,9 @@ typedef struct {
 typedef struct cs_server_s* cs_server_t;
 
 /* Start `workers` (1..64) worker threads with a device-memory budget of
- * hbm_budget_bytes for the jobs in flight. */
+ * hbm_budget_bytes for the jobs in flight.  Raises the release threshold of
+ * the device's default stream-ordered memory pool to the budget (if lower) so
+ * that freed job memory stays pooled for the process. */
 cs_status cs_server_create(int32_t workers, int64_t hbm_budget_bytes, cs_server_t* out);
 
 /* Queue one job; returns at once with its ticket.  The request is checked

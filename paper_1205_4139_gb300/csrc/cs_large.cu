@@ -27,6 +27,9 @@
 // finished instance makes every later kernel of that instance return at
 // once.
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "cs_blocks.cuh"
 #include "cs_internal.h"
@@ -191,13 +194,10 @@ __device__ __forceinline__ void build_position_table(short* tab, int lg) {
 // for the C columns i2 of this CTA, v = in (LD_DENSE, stride in_stride),
 // zf_Omega(in) (LD_ZF, in has M entries per instance) or zf_Omega(1)
 // (LD_ONES).  Only the forward transform F is computed here: the adjoint is
-// read off it by index negation in pass 2.  With LD_ZF and ynorm != NULL the
-// CTA also leaves the FP64 sum of |in_m|^2 over the entries it loaded in
-// ynorm[b * gridDim.x + blockIdx.x] (every m is loaded by exactly one CTA).
+// read off it by index negation in pass 2.
 template <class E, bool DFT, int LD>
 __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restrict__ in, int64_t in_stride,
-                                                   E* __restrict__ out, const LState* __restrict__ st,
-                                                   double* __restrict__ ynorm) {
+                                                   E* __restrict__ out, const LState* __restrict__ st) {
   constexpr int C = tile_c<E>(), LC = log_tile_c<E>();
   extern __shared__ __align__(16) unsigned char sm[];
   E* buf = (E*)sm;
@@ -215,7 +215,6 @@ __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restric
     for (int q = threadIdx.x; q < tot; q += kLT)
       cp_async_elem(buf + (q & (C - 1)) * cs + swz<E>(q >> LC), src + c0 + (q & (C - 1)) + ((q >> LC) << n2));
   } else {  // zero-filled gathers through the slot map, kU in flight per thread
-    double yy = 0.0;
     for (int q0 = threadIdx.x; q0 < tot; q0 += kU * kLT) {
       int m[kU];
 #pragma unroll
@@ -226,23 +225,13 @@ __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restric
       E v[kU];
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
-        if constexpr (LD == LD_ZF) {
-          v[u] = m[u] >= 0 ? src[m[u]] : zero<E>();
-          if (ynorm) yy += norm2(to_w(v[u]));
-        } else {
-          v[u] = m[u] >= 0 ? one_e<E>() : zero<E>();
-        }
+        if constexpr (LD == LD_ZF) v[u] = m[u] >= 0 ? src[m[u]] : zero<E>();
+        else v[u] = m[u] >= 0 ? one_e<E>() : zero<E>();
       }
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         const int q = q0 + u * kLT;
         if (q < tot) buf[(q & (C - 1)) * cs + swz<E>(q >> LC)] = v[u];
-      }
-    }
-    if constexpr (LD == LD_ZF) {
-      if (ynorm) {
-        const double t = block_sum0(yy, (double*)(sm + L.red));
-        if (threadIdx.x == 0) ynorm[b * gridDim.x + blockIdx.x] = t;
       }
     }
   }
@@ -578,21 +567,33 @@ __device__ __forceinline__ int reduce_partials(const V* pv, const int* pj, int n
   return *sj;
 }
 
-// grid (G, batch); dynamic smem: K FP64 elements (the Gram column g)
+// ||y||^2 shares: CTA g of instance b sums |y_m|^2 in FP64 over its chunk of m
 template <class E>
-__global__ void __launch_bounds__(kLT) lls_u_kernel(LOmpArgs<E> a, int nparts) {
+__global__ void __launch_bounds__(kLT) lynorm_kernel(const E* __restrict__ y, int M, double* __restrict__ ypart,
+                                                     int nyp) {
+  __shared__ double red[kLT / 32];
+  const int64_t b = blockIdx.y;
+  const int m0 = (int)(((int64_t)M * blockIdx.x) / nyp), m1 = (int)(((int64_t)M * (blockIdx.x + 1)) / nyp);
+  double t = 0.0;
+  for (int m = m0 + threadIdx.x; m < m1; m += kLT) t += norm2(to_w(y[b * (int64_t)M + m]));
+  t = block_sum0(t, red);
+  if (threadIdx.x == 0) ypart[b * nyp + blockIdx.x] = t;
+}
+
+// Phase u of the append for CTA gi of G on instance b; returns false when the
+// instance is finished (or was already), uniformly over the CTA.
+// gk: K FP64 elements of shared memory (the Gram column g).
+template <class E>
+__device__ bool ls_u_phase(const LOmpArgs<E>& a, int nparts, int G, int gi, int64_t b,
+                           typename FT<E>::W* gk) {
   using W = typename FT<E>::W;
   using V = typename NormT<E>::V;
   constexpr bool DFT = FT<E>::C;
-  extern __shared__ __align__(16) unsigned char sm[];
-  W* gk = (W*)sm;
   __shared__ V rv[34], sv;
   __shared__ int rj[34], sj;
   __shared__ double red[kLT / 32];
-  const int64_t b = blockIdx.y;
-  const int G = gridDim.x, gi = blockIdx.x;
   LState* S = a.st + b;
-  if (S->done) return;
+  if (S->done) return false;
   const int N = a.P.N, K = a.K, p = S->p;
   // step 3: the column with the largest |h(j)|^2
   const int l = reduce_partials(a.part_v + b * a.nparts, a.part_j + b * a.nparts, nparts, rv, rj, &sv, &sj);
@@ -607,12 +608,12 @@ __global__ void __launch_bounds__(kLT) lls_u_kernel(LOmpArgs<E> a, int nparts) {
     ynorm2 = red[0];
     if (!(ynorm2 > 0.0) || K == 0) {  // zero measurement (or K = 0): no iteration
       if (gi == 0) lwrite_outputs(a, b, 0, ynorm2, ynorm2);
-      return;
+      return false;
     }
   }
   if (l < 0) {  // no candidate column left
     if (gi == 0) lwrite_outputs(a, b, p, ynorm2, p == 0 ? ynorm2 : S->rn2);
-    return;
+    return false;
   }
   if (gi == 0 && threadIdx.x == 0) {
     S->pad1 = l;
@@ -661,15 +662,15 @@ __global__ void __launch_bounds__(kLT) lls_u_kernel(LOmpArgs<E> a, int nparts) {
     tb[1] = s1;
     tb[2] = s2;
   }
+  return true;
 }
 
-// grid (G, batch), same G as the lls_u_kernel launch before it
+// Phase w of the append for CTA gi of G on instance b (after phase u of all
+// G CTAs).
 template <class E>
-__global__ void __launch_bounds__(kLT) lls_w_kernel(LOmpArgs<E> a) {
+__device__ void ls_w_phase(const LOmpArgs<E>& a, int G, int gi, int64_t b) {
   using W = typename FT<E>::W;
   __shared__ int ticket;
-  const int64_t b = blockIdx.y;
-  const int G = gridDim.x, gi = blockIdx.x;
   LState* S = a.st + b;
   if (S->done) return;
   const int N = a.P.N, K = a.K, p = S->p, l = S->pad1;
@@ -745,6 +746,28 @@ __global__ void __launch_bounds__(kLT) lls_w_kernel(LOmpArgs<E> a) {
   if (threadIdx.x == 0) S->pad0 = 0;
 }
 
+// grid (G, batch); dynamic smem: K FP64 elements (the Gram column g)
+template <class E>
+__global__ void __launch_bounds__(kLT) lls_u_kernel(LOmpArgs<E> a, int nparts) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  ls_u_phase(a, nparts, (int)gridDim.x, (int)blockIdx.x, (int64_t)blockIdx.y, (typename FT<E>::W*)sm);
+}
+
+// grid (G, batch), same G as the lls_u_kernel launch before it
+template <class E>
+__global__ void __launch_bounds__(kLT) lls_w_kernel(LOmpArgs<E> a) {
+  ls_w_phase(a, (int)gridDim.x, (int)blockIdx.x, (int64_t)blockIdx.y);
+}
+
+// G = 1: both phases in one launch (one CTA per instance)
+template <class E>
+__global__ void __launch_bounds__(kLT) lls_one_kernel(LOmpArgs<E> a, int nparts) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  if (!ls_u_phase(a, nparts, 1, 0, (int64_t)blockIdx.y, (typename FT<E>::W*)sm)) return;
+  __syncthreads();  // u, the shares and the state written by phase u are visible to the whole CTA
+  ls_w_phase(a, 1, 0, (int64_t)blockIdx.y);
+}
+
 // CTAs per instance for the least squares at p columns: about 8192 complex
 // FP64 multiply-adds each, at most gmax
 inline int ls_ctas(int p, int gmax) {
@@ -756,20 +779,39 @@ inline int ls_ctas(int p, int gmax) {
 
 
 // ------------------------------------------------------------- launchers
+// Raises a kernel's dynamic shared-memory limit once per (device, kernel):
+// the attribute persists, and the per-iteration launches of the OMP loop
+// should not pay a driver call each.
 template <class K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set_to;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_pair(dev, (const void*)kernel);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const auto it = set_to.find(key);
+    if (it != set_to.end() && it->second >= bytes) return cudaSuccess;
+  }
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& v = set_to[key];
+    if (bytes > v) v = bytes;
+  }
+  return e;
 }
 
 template <class E, bool DFT, int LD>
 cudaError_t run_col(const LDev<E>& P, const E* in, int64_t in_stride, E* out, const LState* st, int64_t batch,
-                    cudaStream_t s, double* ynorm = nullptr) {
+                    cudaStream_t s) {
   const size_t smem = pass_layout<E>(1 << P.n1).total;
   cudaError_t e = allow_smem(lcol_kernel<E, DFT, LD>, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((1u << P.n2) / tile_c<E>(), (unsigned)batch);
-  lcol_kernel<E, DFT, LD><<<grid, kLT, smem, s>>>(P, in, in_stride, out, st, ynorm);
+  lcol_kernel<E, DFT, LD><<<grid, kLT, smem, s>>>(P, in, in_stride, out, st);
   return cudaGetLastError();
 }
 
@@ -903,7 +945,10 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
   L.lam = o;  o = al16(o + (size_t)batch * Kc * sizeof(int));
   L.pv = o;   o = al16(o + (size_t)batch * L.nparts * sizeof(V));
   L.pj = o;   o = al16(o + (size_t)batch * L.nparts * sizeof(int));
-  L.nyp = (1 << P.n2) / tile_c<E>();
+  {  // CTAs of the ||y||^2 kernel: about 8192 entries each
+    const int64_t g = ((int64_t)P.M + 8191) / 8192;
+    L.nyp = (int)(g < 1 ? 1 : (g > 512 ? 512 : g));
+  }
   L.yp = o;   o = al16(o + (size_t)batch * L.nyp * sizeof(double));
   {  // CTAs per instance for the least squares: fill about 4 waves of the GPU
     int64_t g = (4 * 152 + batch - 1) / batch;
@@ -964,7 +1009,9 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
   for (int t = 1; t <= T_end; ++t) {
     int np;
     if (t == 1) {  // h_0 = Phi^H y by one transform (Eq. kernelsumOMP, first case)
-      if ((e = run_col<E, DFT, LD_ZF>(P, A.y, P.M, T, A.st, batch, s, A.ypart)) != cudaSuccess) return e;
+      lynorm_kernel<E><<<dim3((unsigned)L.nyp, (unsigned)batch), kLT, 0, s>>>(A.y, P.M, A.ypart, L.nyp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = run_col<E, DFT, LD_ZF>(P, A.y, P.M, T, A.st, batch, s)) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_H>(P, T, DFT, isq, A.h0, nullptr, nullptr, A.part_v, A.part_j, L.nparts, A.st,
                                      batch, s)) != cudaSuccess)
         return e;
@@ -986,9 +1033,13 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
       np = rp;
     }
     const dim3 lg((unsigned)ls_ctas(t - 1, L.gmax), (unsigned)batch);
-    lls_u_kernel<E><<<lg, kLT, ls_smem, s>>>(A, np);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    lls_w_kernel<E><<<lg, kLT, 0, s>>>(A);
+    if (lg.x == 1) {
+      lls_one_kernel<E><<<lg, kLT, ls_smem, s>>>(A, np);
+    } else {
+      lls_u_kernel<E><<<lg, kLT, ls_smem, s>>>(A, np);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      lls_w_kernel<E><<<lg, kLT, 0, s>>>(A);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -236,6 +236,16 @@ extern "C" cs_status cs_server_create(int32_t workers, int64_t hbm_budget_bytes,
   }
   S->budget = hbm_budget_bytes;
   S->t0 = std::chrono::steady_clock::now();
+  // Keep up to the budget of freed job memory in the device's stream-ordered
+  // pool instead of returning it to the driver at every synchronisation, so
+  // that admitting a job reuses memory rather than allocating it anew.
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, S->device) == cudaSuccess) {
+    uint64_t cur = 0;
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur);
+    uint64_t want = (uint64_t)hbm_budget_bytes;
+    if (want > cur) cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &want);
+  }
   for (int i = 0; i < workers; ++i) S->workers.emplace_back(worker, S);
   *out = S;
   return CS_OK;
