@@ -94,6 +94,26 @@ typedef struct {
 cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind,
                          int32_t prec, void* stream, cs_plan_t* out);
 
+/* Storage of the correlation kernel vector (the paper's storage remarks,
+ * Sec. III-B), chosen at plan creation; results are those of the full
+ * vector up to FP rounding (CS_PLAN_C_INT: bit for bit):
+ *   CS_PLAN_C_HALF  DFT: c is conjugate symmetric, c(N - d) = conj(c(d)), so
+ *                   only d <= N/2 is stored (half the memory of c)
+ *   CS_PLAN_C_INT   WHT: N c(d) = M - 2 #{i in Omega : popcount(i & d) odd}
+ *                   is an integer, stored exactly as int32 (half the memory
+ *                   of an FP64 c, no FP copy) */
+enum { CS_PLAN_C_HALF = 1u, CS_PLAN_C_INT = 2u };
+
+/* cs_plan_create with storage flags (0 = full vector, as cs_plan_create).
+ * CS_ERR_INVALID for unknown flags, CS_PLAN_C_HALF on a WHT plan,
+ * CS_PLAN_C_INT on a DFT plan, or both. */
+cs_status cs_plan_create_ex(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
+                            uint32_t flags, void* stream, cs_plan_t* out);
+
+/* Device bytes held by the plan's tables (slot map, c in its storage format,
+ * twiddles, status word), not counting the workspace. */
+cs_status cs_plan_memory(cs_plan_t plan, int64_t* table_bytes);
+
 /* Release the plan's device memory (synchronises the device first). */
 cs_status cs_plan_destroy(cs_plan_t plan);
 

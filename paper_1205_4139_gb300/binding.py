@@ -22,7 +22,7 @@ KINDS = {"wht": CS_WHT, "dft": CS_DFT}
 PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 
 # Every function include/csfast.h declares.
-EXPORTS = ["cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
+EXPORTS = ["cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
            "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
            "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy",
            "cs_admit_next", "cs_status_string", "cs_last_error"]
@@ -68,6 +68,8 @@ def load(path: str = LIB_PATH):
     pi32 = ctypes.POINTER(ctypes.c_int32)
     pi64 = ctypes.POINTER(ctypes.c_int64)
     L.cs_plan_create.argtypes = [i64, pi32, i64, i32, i32, vp, ctypes.POINTER(vp)]
+    L.cs_plan_create_ex.argtypes = [i64, pi32, i64, i32, i32, ctypes.c_uint32, vp, ctypes.POINTER(vp)]
+    L.cs_plan_memory.argtypes = [vp, pi64]
     L.cs_plan_destroy.argtypes = [vp]
     L.cs_plan_info.argtypes = [vp, pi64, pi64, pi32, pi32, pi32]
     L.cs_plan_kernel.argtypes = [vp, vp, i32, vp]
@@ -87,7 +89,7 @@ def load(path: str = LIB_PATH):
     L.cs_server_destroy.argtypes = [vp]
     L.cs_admit_next.argtypes = [pi64, pi32, i32, i64, i64, i32]
     L.cs_admit_next.restype = ctypes.c_int32
-    for f in ("cs_plan_create", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
+    for f in ("cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
               "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
               "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy"):
         getattr(L, f).restype = ctypes.c_int
@@ -130,13 +132,15 @@ def ls_dtype(kind: str):
 class Plan:
     """A plan for Phi = S_Omega A (cs_plan_create)."""
 
-    def __init__(self, N: int, omega, kind: str = "dft", prec: str = "fp32", stream=None):
+    def __init__(self, N: int, omega, kind: str = "dft", prec: str = "fp32", stream=None, c_storage: str = "full"):
+        """c_storage: 'full', 'half' (DFT, CS_PLAN_C_HALF) or 'int' (WHT, CS_PLAN_C_INT)."""
         L = load()
         om = np.ascontiguousarray(np.asarray(omega, dtype=np.int32))
         self.N, self.M, self.kind, self.prec = int(N), int(om.size), kind, prec
+        flags = {"full": 0, "half": 1, "int": 2}[c_storage]
         h = ctypes.c_void_p()
-        _check(L.cs_plan_create(self.N, om.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.M, KINDS[kind],
-                                PRECS[prec], _stream(stream), ctypes.byref(h)))
+        _check(L.cs_plan_create_ex(self.N, om.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.M, KINDS[kind],
+                                   PRECS[prec], flags, _stream(stream), ctypes.byref(h)))
         self._h = h
         self.dtype = working_dtype(kind, prec)
 
@@ -157,6 +161,12 @@ class Plan:
         _check(load().cs_plan_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(k), ctypes.byref(p),
                                    ctypes.byref(ts)))
         return {"N": n.value, "M": m.value, "kind": k.value, "prec": p.value, "t_switch_default": ts.value}
+
+    def memory(self) -> int:
+        """Device bytes of the plan's tables (cs_plan_memory)."""
+        b = ctypes.c_int64()
+        _check(load().cs_plan_memory(self._h, ctypes.byref(b)))
+        return b.value
 
     def tune(self, y, K: int, rel_tol: float = 1e-6, stream=None) -> tuple[int, dict]:
         """cs_plan_tune: measure the hybrid switch point on (batch, M) y; returns

@@ -23,6 +23,8 @@ struct cs_plan_s {
   void* d_tw32 = nullptr;
   void* d_c64 = nullptr;
   void* d_c32 = nullptr;
+  int* d_ci = nullptr;      // CFMT_INT: N c(d)
+  size_t table_bytes = 0;   // device bytes of the plan's tables (cs_plan_memory)
   void* d_lt64 = nullptr;   // large plans: four-step tables (FP64)
   void* d_lt32 = nullptr;   // large plans: four-step tables (FP32)
   int* d_status = nullptr;  // kernel-detected errors (cs_plan_status)
@@ -73,7 +75,8 @@ static int plan_switch(const cs_plan_s* p) { return p->t_switch_tuned >= 0 ? p->
 
 static void plan_free(cs_plan_s* p) {
   if (!p) return;
-  void* bufs[] = {p->d_slot, p->d_tw64, p->d_tw32, p->d_c64, p->d_c32, p->d_lt64, p->d_lt32, p->d_status, p->ws};
+  void* bufs[] = {p->d_slot, p->d_tw64, p->d_tw32, p->d_c64, p->d_c32, p->d_ci, p->d_lt64, p->d_lt32, p->d_status,
+                  p->ws};
   for (void* b : bufs) {
     if (!b) continue;
     if (p->ordered) cudaFreeAsync(b, p->home);
@@ -85,6 +88,7 @@ static void plan_free(cs_plan_s* p) {
 // Device allocation for a plan: plain, or stream-ordered on its home stream
 // (no device-wide synchronisation when it is released).
 static cudaError_t plan_alloc(cs_plan_s* p, void** ptr, size_t bytes) {
+  p->table_bytes += bytes;
   return p->ordered ? cudaMallocAsync(ptr, bytes, p->home) : cudaMalloc(ptr, bytes);
 }
 
@@ -100,9 +104,12 @@ static cs_status ensure_ws(cs_plan_s* plan, size_t need, cudaStream_t st) {
 }
 
 static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
-                                  void* stream, bool ordered, cs_plan_t* out) {
+                                  uint32_t flags, void* stream, bool ordered, cs_plan_t* out) {
   if (!out) return CS_ERR_INVALID;
   *out = nullptr;
+  if (flags & ~(uint32_t)(CS_PLAN_C_HALF | CS_PLAN_C_INT)) return CS_ERR_INVALID;
+  if ((flags & CS_PLAN_C_HALF) && kind != CS_DFT) return CS_ERR_INVALID;
+  if ((flags & CS_PLAN_C_INT) && kind != CS_WHT) return CS_ERR_INVALID;
   if (kind != CS_WHT && kind != CS_DFT) return CS_ERR_INVALID;
   if (prec != CS_FP64 && prec != CS_FP32) return CS_ERR_INVALID;
   if (N < 1 || (N & (N - 1))) return CS_ERR_INVALID;
@@ -134,6 +141,7 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
   p->v.n1 = large ? logN / 2 : 0;
   p->v.n2 = large ? logN - logN / 2 : 0;
   p->v.wsh = large ? (logN + 1) / 2 : 0;
+  p->v.cfmt = (flags & CS_PLAN_C_HALF) ? CFMT_HALF : ((flags & CS_PLAN_C_INT) ? CFMT_INT : CFMT_FULL);
   // Sec. IV excessive point under the Table I flop model
   p->t_switch_default = kind == CS_DFT ? 1 + (5 * logN) / 6 : 1 + logN;
 
@@ -169,8 +177,11 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
     PLAN_TRY(plan_alloc(p, &p->d_lt64, nt * sizeof(double2)), "cudaMalloc four-step tables");
     if (prec == CS_FP32) PLAN_TRY(plan_alloc(p, &p->d_lt32, nt * sizeof(float2)), "cudaMalloc four-step tables");
   }
-  PLAN_TRY(plan_alloc(p, &p->d_c64, (size_t)N * wb), "cudaMalloc c");
-  if (prec == CS_FP32) PLAN_TRY(plan_alloc(p, &p->d_c32, (size_t)N * wb / 2), "cudaMalloc c");
+  const int cfmt = p->v.cfmt;
+  const size_t nc = cfmt == CFMT_HALF ? (size_t)N / 2 + 1 : (cfmt == CFMT_INT ? 0 : (size_t)N);
+  if (nc) PLAN_TRY(plan_alloc(p, &p->d_c64, nc * wb), "cudaMalloc c");
+  if (nc && prec == CS_FP32) PLAN_TRY(plan_alloc(p, &p->d_c32, nc * wb / 2), "cudaMalloc c");
+  if (cfmt == CFMT_INT) PLAN_TRY(plan_alloc(p, (void**)&p->d_ci, (size_t)N * sizeof(int)), "cudaMalloc c");
   PLAN_TRY(plan_alloc(p, (void**)&p->d_status, sizeof(int)), "cudaMalloc status");
   PLAN_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st), "clear status");
   p->v.slot = p->d_slot;
@@ -181,18 +192,39 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
   p->v.status = p->d_status;
   p->v.lt64 = p->d_lt64;
   p->v.lt32 = p->d_lt32;
-  if (!large) {
-    if (kind == CS_DFT) PLAN_TRY(launch_twiddles(p->v, p->d_tw64, p->d_tw32, st), "twiddle kernel");
-    PLAN_TRY(launch_kernel_vector(p->v, p->d_c64, p->d_c32, st), "kernel-vector kernel");
-    PLAN_TRY(cudaStreamSynchronize(st), "plan synchronize");
-  } else {
+  p->v.ci = p->d_ci;
+  // c in FP64, full length: into the plan's own buffer (CFMT_FULL) or a
+  // scratch vector that is then put into the plan's storage format
+  {
+    const size_t tb0 = p->table_bytes;
+    e = cudaSuccess;
+    void* full = cfmt == CFMT_FULL ? p->d_c64 : nullptr;
     void* tmp = nullptr;
-    PLAN_TRY(large_tables(p->v, p->d_lt64, p->d_lt32, st), "four-step tables");
-    PLAN_TRY(plan_alloc(p, &tmp, (size_t)N * wb), "cudaMalloc plan scratch");
-    e = large_kernel_vector(p->v, p->d_c64, p->d_c32, tmp, st);
-    if (ordered) cudaFreeAsync(tmp, st);
+    if (!full) PLAN_TRY(plan_alloc(p, &full, (size_t)N * wb), "cudaMalloc plan scratch");
+    if (large) PLAN_TRY(plan_alloc(p, &tmp, (size_t)N * wb), "cudaMalloc plan scratch");
+    if (!large) {
+      if (kind == CS_DFT) e = launch_twiddles(p->v, p->d_tw64, p->d_tw32, st);
+      if (e == cudaSuccess) e = launch_kernel_vector(p->v, full, st);
+    } else {
+      e = large_tables(p->v, p->d_lt64, p->d_lt32, st);
+      if (e == cudaSuccess) e = large_kernel_vector(p->v, full, tmp, st);
+    }
+    if (e == cudaSuccess) {
+      if (cfmt == CFMT_FULL) {
+        if (p->d_c32) e = launch_round(kind == CS_DFT, p->d_c64, p->d_c32, (int)N, st);
+      } else {
+        e = launch_compress_c(p->v, full, p->d_c64, p->d_c32, p->d_ci, st);
+      }
+    }
+    void* scratch[] = {cfmt == CFMT_FULL ? nullptr : full, tmp};
+    if (ordered)
+      for (void* b : scratch)
+        if (b) cudaFreeAsync(b, st);
     const cudaError_t e2 = cudaStreamSynchronize(st);
-    if (!ordered) cudaFree(tmp);
+    if (!ordered)
+      for (void* b : scratch)
+        if (b) cudaFree(b);
+    p->table_bytes = tb0;  // scratch is not part of the plan
     PLAN_TRY(e, "kernel-vector kernels");
     PLAN_TRY(e2, "plan synchronize");
   }
@@ -203,7 +235,18 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
 
 extern "C" cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
                                     void* stream, cs_plan_t* out) {
-  return plan_create_impl(N, omega_host, M, kind, prec, stream, false, out);
+  return plan_create_impl(N, omega_host, M, kind, prec, 0u, stream, false, out);
+}
+
+extern "C" cs_status cs_plan_create_ex(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
+                                       uint32_t flags, void* stream, cs_plan_t* out) {
+  return plan_create_impl(N, omega_host, M, kind, prec, flags, stream, false, out);
+}
+
+extern "C" cs_status cs_plan_memory(cs_plan_t plan, int64_t* table_bytes) {
+  if (!plan || !table_bytes) return CS_ERR_INVALID;
+  *table_bytes = (int64_t)plan->table_bytes;
+  return CS_OK;
 }
 
 namespace csf {
@@ -211,7 +254,7 @@ namespace csf {
 // that creating and releasing one never synchronises the device.
 cs_status plan_create_ordered(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
                               cudaStream_t stream, cs_plan_t* out) {
-  return plan_create_impl(N, omega_host, M, kind, prec, stream, true, out);
+  return plan_create_impl(N, omega_host, M, kind, prec, 0u, stream, true, out);
 }
 // Queues the release of a stream-ordered plan's buffers on its stream.
 void plan_release_ordered(cs_plan_t plan) { plan_free(plan); }
@@ -280,6 +323,10 @@ extern "C" cs_status cs_plan_kernel(cs_plan_t plan, void* c_dev, int32_t prec, v
   if (!plan || !c_dev) return CS_ERR_INVALID;
   if (prec != CS_FP64 && prec != CS_FP32) return CS_ERR_INVALID;
   const size_t n = (size_t)plan->v.N;
+  if (plan->v.cfmt != CFMT_FULL) {
+    CS_CUDA(launch_expand_c(plan->v, c_dev, prec == CS_FP32, (cudaStream_t)stream), "expand c");
+    return CS_OK;
+  }
   if (prec == CS_FP64) {
     CS_CUDA(cudaMemcpyAsync(c_dev, plan->d_c64, n * elem_bytes(plan->kind, CS_FP64), cudaMemcpyDeviceToDevice,
                             (cudaStream_t)stream),

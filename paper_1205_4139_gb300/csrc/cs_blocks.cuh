@@ -20,9 +20,46 @@ struct PlanDev {
   int N, logN, M;
   const int* __restrict__ slot;  // [N]: m if position holds row Omega_m, else -1
   const E* __restrict__ tw;      // DIF twiddles in the working precision (DFT only)
-  const E* __restrict__ c;       // correlation kernel vector, working precision [N]
-  const typename FT<E>::W* __restrict__ c64;  // correlation kernel vector, FP64 [N]
+  const E* __restrict__ c;       // correlation kernel vector, working precision (storage format cfmt)
+  const typename FT<E>::W* __restrict__ c64;  // correlation kernel vector, FP64 (storage format cfmt)
+  int cfmt;                      // CFMT_FULL, CFMT_HALF (DFT) or CFMT_INT (WHT)
+  const int* __restrict__ ci;    // CFMT_INT: N c(d), exact integers
 };
+
+// v 2^-logN in T, exact for |v| < 2^24 (FP32) or 2^53 (FP64): the integer
+// converts exactly and the power of two scales exactly
+template <class T> __device__ __forceinline__ T int_scaled(int v, int logN);
+template <> __device__ __forceinline__ float int_scaled<float>(int v, int logN) {
+  return __int2float_rn(v) * __int_as_float((127 - logN) << 23);
+}
+template <> __device__ __forceinline__ double int_scaled<double>(int v, int logN) {
+  return __int2double_rn(v) * __longlong_as_double((long long)(1023 - logN) << 52);
+}
+template <> __device__ __forceinline__ float2 int_scaled<float2>(int v, int logN) {
+  return make_float2(int_scaled<float>(v, logN), 0.f);
+}
+template <> __device__ __forceinline__ double2 int_scaled<double2>(int v, int logN) {
+  return make_double2(int_scaled<double>(v, logN), 0.0);
+}
+
+// c(d), 0 <= d < N, from a vector in storage format `fmt` (s: the full or
+// half vector in T; ci: the integers N c(d); N = 2^logN).  For CFMT_INT the
+// scaling by 2^-logN is exact.
+template <class T>
+__device__ __forceinline__ T c_entry(int fmt, const T* __restrict__ s, const int* __restrict__ ci, int N, int logN,
+                                     int d) {
+  if (fmt == CFMT_HALF) return d <= (N >> 1) ? __ldg(s + d) : conjv(__ldg(s + (N - d)));
+  if (fmt == CFMT_INT) return int_scaled<T>(__ldg(ci + d), logN);
+  return __ldg(s + d);
+}
+template <class E>
+__device__ __forceinline__ typename FT<E>::W c64_at(const PlanDev<E>& P, int d) {
+  return c_entry(P.cfmt, P.c64, P.ci, P.N, P.logN, d);
+}
+template <class E>
+__device__ __forceinline__ E cw_at(const PlanDev<E>& P, int d) {
+  return c_entry(P.cfmt, P.c, P.ci, P.N, P.logN, d);
+}
 
 template <class E>
 inline PlanDev<E> plan_dev(const PlanView& P) {
@@ -35,6 +72,8 @@ inline PlanDev<E> plan_dev(const PlanView& P) {
   d.tw = (const E*)(f32 ? P.tw32 : P.tw64);
   d.c = (const E*)(f32 ? P.c32 : P.c64);
   d.c64 = (const typename FT<E>::W*)P.c64;
+  d.cfmt = P.cfmt;
+  d.ci = P.ci;
   return d;
 }
 
@@ -195,7 +234,7 @@ __host__ __device__ inline bool kernel_doubled(int N) {
 template <class E, bool DFT>
 __device__ void load_kernel_vector(const Grp& g, E* cb, const PlanDev<E>& P, bool doubled) {
   const int n = (DFT && doubled) ? 2 * P.N : P.N;
-  for (int i = g.tid; i < n; i += g.n) cb[i] = __ldg(P.c + (i & (P.N - 1)));
+  for (int i = g.tid; i < n; i += g.n) cb[i] = cw_at(P, i & (P.N - 1));
   g.sync();
 }
 

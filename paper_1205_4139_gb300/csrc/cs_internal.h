@@ -30,7 +30,14 @@ struct PlanView {
   int n1, n2, wsh;
   const void* lt64;
   const void* lt32;
+  // storage of c: CFMT_FULL c64 / c32 hold c(0..N-1); CFMT_HALF (DFT) hold
+  // c(0..N/2) and c(N - d) = conj(c(d)); CFMT_INT (WHT) ci holds the exact
+  // integers N c(d) and c64 / c32 are unused
+  int cfmt;
+  const int* ci;
 };
+
+enum { CFMT_FULL = 0, CFMT_HALF = 1, CFMT_INT = 2 };
 
 // Bits of the device status word.
 constexpr int kStatusPhaseBound = 1;  // the OMP kernel's phase loop hit its bound
@@ -62,7 +69,10 @@ struct PursuitLaunch {
 cudaError_t launch_twiddles(const PlanView& P, void* tw64, void* tw32, cudaStream_t st);
 cudaError_t launch_twiddles_log(int logN, void* tw64, void* tw32, cudaStream_t st);
 cudaError_t launch_round(bool dft, const void* c64, void* c32, int n, cudaStream_t st);
-cudaError_t launch_kernel_vector(const PlanView& P, void* c64, void* c32, cudaStream_t st);
+// c from its full FP64 vector into the plan's storage format, and back
+cudaError_t launch_compress_c(const PlanView& P, const void* full64, void* c64, void* c32, int* ci, cudaStream_t st);
+cudaError_t launch_expand_c(const PlanView& P, void* out, bool fp32, cudaStream_t st);
+cudaError_t launch_kernel_vector(const PlanView& P, void* c64_full, cudaStream_t st);
 
 // transforms / correlations
 cudaError_t launch_correlate(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax,
@@ -78,7 +88,7 @@ cudaError_t launch_omp(const PlanView& P, const OmpLaunch& a, void* ws, int grid
 
 // large plans (cs_large.cu)
 cudaError_t large_tables(const PlanView& P, void* lt64, void* lt32, cudaStream_t st);
-cudaError_t large_kernel_vector(const PlanView& P, void* c64, void* c32, void* tmp, cudaStream_t st);
+cudaError_t large_kernel_vector(const PlanView& P, void* c64_full, void* tmp, cudaStream_t st);
 size_t large_correlate_ws(const PlanView& P, int64_t batch);
 cudaError_t large_correlate(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax, void* ws,
                             cudaStream_t st);

@@ -76,10 +76,56 @@ static cudaError_t kv_impl(const PlanView& P, void* c64, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_kernel_vector(const PlanView& P, void* c64, void* c32, cudaStream_t st) {
-  cudaError_t e = P.dft ? kv_impl<double2>(P, c64, st) : kv_impl<double>(P, c64, st);
-  if (e != cudaSuccess || !c32) return e;
-  return launch_round(P.dft, c64, c32, P.N, st);
+cudaError_t launch_kernel_vector(const PlanView& P, void* c64_full, cudaStream_t st) {
+  return P.dft ? kv_impl<double2>(P, c64_full, st) : kv_impl<double>(P, c64_full, st);
+}
+
+// Storage formats of c (the paper's storage remarks, Sec. III-B): the DFT
+// kernel vector is conjugate symmetric, c(N - d) = conj(c(d)), so d <= N/2
+// suffices (CFMT_HALF); the WHT kernel vector takes the values
+// (M - 2 #{i in Omega : popcount(i & d) odd}) / N, so N c(d) is an integer,
+// stored exactly (CFMT_INT).
+template <class W, class E>
+__global__ void compress_c_kernel(int fmt, const W* __restrict__ full, int N, int logN, W* c64, E* c32, int* ci) {
+  const int n = fmt == CFMT_HALF ? (N >> 1) + 1 : N;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
+    const W v = full[d];
+    if (fmt == CFMT_INT) {
+      ci[d] = (int)llrint(ldexp(re(v), logN));
+    } else {
+      c64[d] = v;
+      if (c32) c32[d] = from_w<E>(v);
+    }
+  }
+}
+
+template <class W, class E>
+__global__ void expand_c_kernel(PlanDev<E> P, W* out64, E* out32) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < P.N; d += gridDim.x * blockDim.x) {
+    if (out64) out64[d] = c64_at(P, d);
+    if (out32) out32[d] = from_w<E>(c64_at(P, d));
+  }
+}
+
+cudaError_t launch_compress_c(const PlanView& P, const void* full64, void* c64, void* c32, int* ci, cudaStream_t st) {
+  if (P.dft) compress_c_kernel<double2, float2><<<64, kThreads, 0, st>>>(P.cfmt, (const double2*)full64, P.N, P.logN,
+                                                                         (double2*)c64, (float2*)c32, ci);
+  else compress_c_kernel<double, float><<<64, kThreads, 0, st>>>(P.cfmt, (const double*)full64, P.N, P.logN,
+                                                                 (double*)c64, (float*)c32, ci);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_c(const PlanView& P, void* out, bool fp32, cudaStream_t st) {
+  if (P.dft) {
+    PlanDev<float2> d = plan_dev<float2>(P);
+    expand_c_kernel<double2, float2><<<64, kThreads, 0, st>>>(d, fp32 ? nullptr : (double2*)out,
+                                                              fp32 ? (float2*)out : nullptr);
+  } else {
+    PlanDev<float> d = plan_dev<float>(P);
+    expand_c_kernel<double, float><<<64, kThreads, 0, st>>>(d, fp32 ? nullptr : (double*)out,
+                                                            fp32 ? (float*)out : nullptr);
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------- conventional correlation

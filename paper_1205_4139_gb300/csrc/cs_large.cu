@@ -55,8 +55,10 @@ struct LDev {
   const E* __restrict__ tw2;     // DIF twiddles of the N2 chain
   const E* __restrict__ wlo;     // w_N^m, m < 2^wsh
   const E* __restrict__ whi;     // w_N^(m 2^wsh), m < N / 2^wsh
-  const E* __restrict__ c;       // kernel vector, working precision
-  const W* __restrict__ c64;     // kernel vector, FP64
+  const E* __restrict__ c;       // kernel vector, working precision (storage format cfmt)
+  const W* __restrict__ c64;     // kernel vector, FP64 (storage format cfmt)
+  int cfmt;                      // CFMT_FULL, CFMT_HALF (DFT) or CFMT_INT (WHT)
+  const int* __restrict__ ci;    // CFMT_INT: N c(d)
 };
 
 template <class E>
@@ -78,6 +80,8 @@ LDev<E> ldev(const PlanView& P) {
   d.whi = t ? t + N1 + N2 + (1 << P.wsh) : nullptr;
   d.c = (const E*)(f32 ? P.c32 : P.c64);
   d.c64 = (const typename FT<E>::W*)P.c64;
+  d.cfmt = P.cfmt;
+  d.ci = P.ci;
   return d;
 }
 
@@ -369,7 +373,7 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
 // this CTA (Eq. kernelsumOMP); lam / x of instance b start at b * kstride.
 // Stores h if h != NULL; the arg-max over j with a clear bit (all j if
 // bits == NULL) goes to the partial.
-template <class E, bool DFT>
+template <class E, bool DFT, int CF>
 __global__ void __launch_bounds__(kLT) lfast_kernel(LDev<E> P, const E* __restrict__ h0,
                                                     const int* __restrict__ lam, const E* __restrict__ xw, int s,
                                                     int64_t kstride, const uint32_t* __restrict__ bits,
@@ -403,7 +407,11 @@ __global__ void __launch_bounds__(kLT) lfast_kernel(LDev<E> P, const E* __restri
     for (int e = 0; e < kFastCH; ++e) {
       const int j = j0 + e * kLT;
       const int d = DFT ? ((j - l) & (N - 1)) : (j ^ l);
-      acc[e] = fnms(acc[e], xk, __ldg(P.c + d));
+      E cv;
+      if constexpr (CF == CFMT_HALF) cv = d <= (N >> 1) ? __ldg(P.c + d) : conjv(__ldg(P.c + (N - d)));
+      else if constexpr (CF == CFMT_INT) cv = int_scaled<E>(__ldg(P.ci + d), P.logN);
+      else cv = __ldg(P.c + d);
+      acc[e] = fnms(acc[e], xk, cv);
     }
   }
   const uint32_t* bb = bits ? bits + b * (int64_t)(N >> 5) : nullptr;
@@ -627,7 +635,7 @@ __device__ bool ls_u_phase(const LOmpArgs<E>& a, int nparts, int G, int gi, int6
   const int* lam = a.lam + b * K;
   for (int k = threadIdx.x; k < r1; k += kLT) {
     const int d = DFT ? ((lam[k] - l) & (N - 1)) : (lam[k] ^ l);
-    gk[k] = a.P.c64[d];
+    gk[k] = c_entry(a.P.cfmt, a.P.c64, a.P.ci, N, a.P.logN, d);
   }
   __syncthreads();
   const W* B = a.B + b * (((int64_t)K * (K + 1)) >> 1);
@@ -684,7 +692,7 @@ __device__ void ls_w_phase(const LOmpArgs<E>& a, int G, int gi, int64_t b) {
     ar += tb[1];
     ai += tb[2];
   }
-  const double d2 = re(a.P.c64[0]) - an;
+  const double d2 = re(c_entry(a.P.cfmt, a.P.c64, a.P.ci, N, a.P.logN, 0)) - an;
   if (!(d2 > 1e-10 * ((double)a.P.M / (double)N))) {  // column dependent on Lambda: not added
     if (gi == 0) lwrite_outputs(a, b, p, ynorm2, rn2);
     return;
@@ -835,10 +843,21 @@ cudaError_t run_fast(const LDev<E>& P, const E* h0, const int* lam, const E* xw,
   using V = typename NormT<E>::V;
   const size_t smem = al16((size_t)s * sizeof(E)) + al16((size_t)s * sizeof(int)) + al16(34 * sizeof(V)) +
                       34 * sizeof(int);
-  cudaError_t e = allow_smem(lfast_kernel<E, DFT>, smem);
-  if (e != cudaSuccess) return e;
   const dim3 grid(P.N / kFastTile, (unsigned)batch);
-  lfast_kernel<E, DFT><<<grid, kLT, smem, strm>>>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st);
+  cudaError_t e;
+  if (DFT && P.cfmt == CFMT_HALF) {
+    if ((e = allow_smem(lfast_kernel<E, DFT, CFMT_HALF>, smem)) != cudaSuccess) return e;
+    lfast_kernel<E, DFT, CFMT_HALF><<<grid, kLT, smem, strm>>>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts,
+                                                               st);
+  } else if (!DFT && P.cfmt == CFMT_INT) {
+    if ((e = allow_smem(lfast_kernel<E, DFT, CFMT_INT>, smem)) != cudaSuccess) return e;
+    lfast_kernel<E, DFT, CFMT_INT><<<grid, kLT, smem, strm>>>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts,
+                                                              st);
+  } else {
+    if ((e = allow_smem(lfast_kernel<E, DFT, CFMT_FULL>, smem)) != cudaSuccess) return e;
+    lfast_kernel<E, DFT, CFMT_FULL><<<grid, kLT, smem, strm>>>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts,
+                                                               st);
+  }
   return cudaGetLastError();
 }
 
@@ -1074,10 +1093,8 @@ cudaError_t large_tables(const PlanView& P, void* lt64, void* lt32, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t large_kernel_vector(const PlanView& P, void* c64, void* c32, void* tmp, cudaStream_t st) {
-  cudaError_t e = P.dft ? kv_t<double2>(P, c64, tmp, st) : kv_t<double>(P, c64, tmp, st);
-  if (e != cudaSuccess || !c32) return e;
-  return launch_round(P.dft, c64, c32, P.N, st);
+cudaError_t large_kernel_vector(const PlanView& P, void* c64_full, void* tmp, cudaStream_t st) {
+  return P.dft ? kv_t<double2>(P, c64_full, tmp, st) : kv_t<double>(P, c64_full, tmp, st);
 }
 
 size_t large_correlate_ws(const PlanView& P, int64_t batch) {

@@ -46,11 +46,11 @@ __device__ void ls_append(const Grp& g, const PlanDev<E>& P, const LsView<E>& v,
   using W = typename FT<E>::W;
   constexpr bool DFT = FT<E>::C;
   const int N = P.N;
-  const double c0 = re(P.c64[0]);                        // c(0) = M/N
+  const double c0 = re(c64_at(P, 0));                    // c(0) = M/N
   const double dep = 1e-10 * ((double)P.M / (double)N);  // dependence threshold on d^2
   for (int k = g.tid; k < p; k += g.n) {
     const int d = DFT ? ((v.lam[k] - l) & (N - 1)) : (v.lam[k] ^ l);
-    v.g[k] = P.c64[d];                                    // G(lambda_k, lambda)
+    v.g[k] = c64_at(P, d);                                // G(lambda_k, lambda)
   }
   g.sync();
   // g <- u = B g; the finishing threads leave |u_k|^2 and conj(u_k) z_k in terms

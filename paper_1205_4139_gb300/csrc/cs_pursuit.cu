@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kPThreads) pursuit_kernel(PursuitArgs<E> a) {
             W gx = W{};
             for (int j = 0; j < kk; ++j) {
               const int d = DFT ? ((T[i] - T[j]) & (N - 1)) : (T[i] ^ T[j]);
-              gx = fmav(gx, a.P.c64[d], lv.g[j]);
+              gx = fmav(gx, c64_at(a.P, d), lv.g[j]);
             }
             acc[1] += re(cmul(xi, gx));
           }
