@@ -223,7 +223,41 @@ def secondary(args, dev, plan, inst, stream, flush):
                                   "paper_flop_model": costmodel.cosamp_fast_ratio(8192, 4)}
     out["large_dft_c64_N4194304_M524288"] = large_single(dev, stream, flush)
     out["serving"] = serving(args.serve_requests)
+    out["uneven_batch"] = uneven(args.uneven_instances)
     return out
+
+
+def _uneven_gen(spec):
+    return synth.uneven_instance(spec)
+
+
+def uneven(n_inst: int, workers: int = 8, budget_gb: float = 64.0):
+    """The uneven batch (BASELINE's third configuration, a sample of it):
+    N = 2^12 .. 2^16, M = N/4 or N/8, K = 8 .. 256, WHT FP32 or DFT complex64,
+    per-instance Omega, noiseless, all submitted at once to the request
+    runtime, which runs them concurrently on `workers` streams (one plan and
+    one solve per instance: not the single persistent launch the
+    configuration describes)."""
+    from paper_1205_4139_gb300 import binding
+    specs = synth.uneven_batch(n_inst, seed=0)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 1)) as pool:
+        data = pool.map(_uneven_gen, specs)
+    srv = binding.Server(workers=workers, budget_bytes=int(budget_gb * (1 << 30)))
+    for sp, (om, yv) in list(zip(specs, data))[:8]:  # warm-up on the first few instances
+        srv.submit(sp["kind"], "fp32", sp["N"], om, yv, sp["K"])
+    srv.wait_all()
+    t0 = time.perf_counter()
+    for sp, (om, yv) in zip(specs, data):
+        srv.submit(sp["kind"], "fp32", sp["N"], om, yv, sp["K"])
+    res = srv.wait_all()
+    wall = time.perf_counter() - t0
+    srv.close()
+    iters = sum(r["iters"] for r in res)
+    return {"workload": f"{n_inst} instances, N=2^12..2^16, M=N/4 or N/8, K=8..256, WHT fp32 / DFT c64, "
+                        "per-instance Omega, noiseless", "workers": workers, "instances": len(res),
+            "failed": sum(1 for r in res if r["status"] != 0 or r["device_error"] != 0),
+            "solves_per_s": len(res) / wall, "correlations_per_s": iters / wall, "wall_s": wall}
 
 
 def _serving_gen(req):
@@ -446,6 +480,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle instances (default one per core)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement")
+    ap.add_argument("--uneven-instances", type=int, default=1024, help="instances of the uneven-batch measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -143,3 +143,28 @@ def serving_instance(req: dict, prec: str = "fp32") -> tuple[np.ndarray, np.ndar
     """(Omega, y) of one serving request (one instance, noiseless)."""
     inst = make_batch(req["kind"], req["N"], req["M"], req["K"], 1, snr_db=None, prec=prec, seed=req["seed"])
     return inst["omega"], inst["Y"][0]
+
+
+# The uneven batch: N = 2^e with e uniform over [log_n_lo, log_n_hi]; M = N/4
+# or N/8 by a coin; K uniform over [k_lo, k_hi]; partial WHT in FP32 or
+# partial DFT in complex64 by a coin; Rademacher or Gaussian nonzeros by a
+# coin; noiseless; each instance with its own Omega and seed.
+def uneven_batch(n: int, seed: int = 0, log_n_lo: int = 12, log_n_hi: int = 16, k_lo: int = 8,
+                 k_hi: int = 256) -> list[dict]:
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        N = 1 << int(rng.integers(log_n_lo, log_n_hi + 1))
+        M = N // (4 if rng.integers(0, 2) else 8)
+        K = int(min(rng.integers(k_lo, k_hi + 1), M))
+        kind = DFT if rng.integers(0, 2) else WHT
+        dist = "rademacher" if rng.integers(0, 2) else "gauss"
+        out.append({"kind": kind, "N": N, "M": M, "K": K, "dist": dist, "seed": seed * 1000003 + i + 1})
+    return out
+
+
+def uneven_instance(spec: dict) -> tuple[np.ndarray, np.ndarray]:
+    """(Omega, y) of one instance of the uneven batch (FP32 working type)."""
+    inst = make_batch(spec["kind"], spec["N"], spec["M"], spec["K"], 1, snr_db=None, dist=spec["dist"],
+                      prec="fp32", seed=spec["seed"])
+    return inst["omega"], inst["Y"][0]
