@@ -3,7 +3,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/csfast.h"
@@ -63,6 +66,20 @@ extern "C" const char* cs_status_string(cs_status s) {
 extern "C" const char* cs_last_error(void) { return g_err; }
 
 namespace csf {
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[std::make_pair(dev, func)];
+  if (cur >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 // accessors for the other translation units of the library
 const PlanView* plan_view(cs_plan_t plan) { return &plan->v; }
 int plan_t_switch_default(cs_plan_t plan) { return plan->t_switch_default; }

@@ -65,6 +65,13 @@ struct PursuitLaunch {
   double* res_out;
 };
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  The limit is a property of the kernel shared by every
+// thread of the process, so it only ever grows, under a lock: callers with
+// different needs (the request runtime's workers) never lower it under one
+// another between setting it and launching.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
+
 // plan construction
 cudaError_t launch_twiddles(const PlanView& P, void* tw64, void* tw32, cudaStream_t st);
 cudaError_t launch_twiddles_log(int logN, void* tw64, void* tw32, cudaStream_t st);

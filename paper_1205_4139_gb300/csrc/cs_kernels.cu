@@ -70,7 +70,7 @@ cudaError_t launch_round(bool dft, const void* c64, void* c32, int n, cudaStream
 template <class W>
 static cudaError_t kv_impl(const PlanView& P, void* c64, cudaStream_t st) {
   const size_t smem = (size_t)P.N * sizeof(W);
-  cudaError_t e = cudaFuncSetAttribute(kernel_vector_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)kernel_vector_kernel<W>, smem);
   if (e != cudaSuccess) return e;
   kernel_vector_kernel<W><<<1, kThreads, smem, st>>>(plan_dev<W>(P), (W*)c64);
   return cudaGetLastError();
@@ -149,7 +149,7 @@ static cudaError_t corr_impl(const PlanView& P, const void* r, int64_t batch, vo
                              cudaStream_t st) {
   using V = typename NormT<E>::V;
   const size_t smem = align16((size_t)P.N * sizeof(E)) + 34 * sizeof(V) + 34 * sizeof(int);
-  cudaError_t e = cudaFuncSetAttribute(correlate_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)correlate_kernel<E>, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -213,7 +213,7 @@ static cudaError_t fast_impl(const PlanView& P, const void* h0, const int32_t* s
   smem = align16(smem + (size_t)s * sizeof(int));
   smem = align16(smem + (size_t)((N + 31) >> 5) * sizeof(uint32_t));
   smem += 34 * sizeof(V) + 34 * sizeof(int);
-  cudaError_t e = cudaFuncSetAttribute(fast_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)fast_kernel<E>, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

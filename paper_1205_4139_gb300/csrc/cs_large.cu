@@ -27,9 +27,6 @@
 // finished instance makes every later kernel of that instance return at
 // once.
 #include <cmath>
-#include <map>
-#include <mutex>
-#include <utility>
 
 #include "cs_blocks.cuh"
 #include "cs_internal.h"
@@ -787,29 +784,9 @@ inline int ls_ctas(int p, int gmax) {
 
 
 // ------------------------------------------------------------- launchers
-// Raises a kernel's dynamic shared-memory limit once per (device, kernel):
-// the attribute persists, and the per-iteration launches of the OMP loop
-// should not pay a driver call each.
 template <class K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  static std::mutex mu;
-  static std::map<std::pair<int, const void*>, size_t> set_to;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const auto key = std::make_pair(dev, (const void*)kernel);
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    const auto it = set_to.find(key);
-    if (it != set_to.end() && it->second >= bytes) return cudaSuccess;
-  }
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) {
-    std::lock_guard<std::mutex> lk(mu);
-    size_t& v = set_to[key];
-    if (bytes > v) v = bytes;
-  }
-  return e;
+  return raise_smem_limit((const void*)kernel, bytes);
 }
 
 template <class E, bool DFT, int LD>

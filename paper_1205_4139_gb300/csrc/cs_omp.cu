@@ -300,7 +300,7 @@ template <class E>
 int grid_t(const PlanView& P, int K, int path, int64_t batch, int* err) {
   const size_t smem = smem_t<E>(P, K, path);
   *err = 0;
-  cudaError_t e = cudaFuncSetAttribute(omp_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)omp_kernel<E>, smem);
   if (e != cudaSuccess) { *err = (int)e; return 0; }
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);

@@ -305,7 +305,7 @@ template <class E>
 int pgrid_t(const PlanView& P, int K, int algo, int fast, int64_t batch, int* err) {
   const size_t smem = psmem_t<E>(P, K, algo, fast);
   *err = 0;
-  cudaError_t e = cudaFuncSetAttribute(pursuit_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)pursuit_kernel<E>, smem);
   if (e != cudaSuccess) { *err = (int)e; return 0; }
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);

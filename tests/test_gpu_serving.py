@@ -134,3 +134,29 @@ def test_refusals():
     with pytest.raises(binding.CsError):  # CoSaMP beyond one-CTA sizes
         srv.submit("dft", "fp32", 1 << 16, inst["omega"], inst["Y"][0], 8, algo="cosamp")
     srv.close()
+
+
+def test_concurrent_small_plans_with_different_shared_memory():
+    """Many one-CTA jobs whose kernels need different amounts of shared
+    memory (N 4096 / 8192, K 8 .. 256, both kinds) on 8 workers: every job
+    succeeds and equals its solve alone (the per-kernel shared-memory limit
+    is only ever raised, so concurrent launches never see it lowered)."""
+    rng = np.random.default_rng(21)
+    specs = []
+    for i in range(48):
+        N = int(rng.choice([4096, 8192]))
+        M = N // int(rng.choice([4, 8]))
+        specs.append(("dft" if i % 2 else "wht", N, M, int(rng.integers(8, 257))))
+    insts = [synth.make_batch(k, N, M, K, 1, snr_db=None, prec="fp32", seed=500 + i)
+             for i, (k, N, M, K) in enumerate(specs)]
+    srv = binding.Server(workers=8, budget_bytes=8 << 30)
+    tickets = [srv.submit(k, "fp32", N, inst["omega"], inst["Y"][0], K)
+               for (k, N, M, K), inst in zip(specs, insts)]
+    res = {r["ticket"]: r for r in srv.wait_all()}
+    srv.close()
+    assert all(res[t]["status"] == 0 and res[t]["device_error"] == 0 for t in tickets)
+    for i in (0, 7, 19, 33):
+        k, N, M, K = specs[i]
+        x0, s0, it0, rn0 = alone((k, "fp32", N, K, "omp", insts[i]))
+        r = res[tickets[i]]
+        assert np.array_equal(r["supp"], s0) and np.array_equal(r["x"], x0) and r["iters"] == it0
