@@ -941,9 +941,9 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
   L.lam = o;  o = al16(o + (size_t)batch * Kc * sizeof(int));
   L.pv = o;   o = al16(o + (size_t)batch * L.nparts * sizeof(V));
   L.pj = o;   o = al16(o + (size_t)batch * L.nparts * sizeof(int));
-  {  // CTAs of the ||y||^2 kernel: about 8192 entries each
-    const int64_t g = ((int64_t)P.M + 8191) / 8192;
-    L.nyp = (int)(g < 1 ? 1 : (g > 512 ? 512 : g));
+  {  // CTAs of the ||y||^2 kernel: about 2048 entries each (its FP64 work spreads over the SMs)
+    const int64_t g = ((int64_t)P.M + 2047) / 2048;
+    L.nyp = (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
   }
   L.yp = o;   o = al16(o + (size_t)batch * L.nyp * sizeof(double));
   {  // CTAs per instance for the least squares: fill about 4 waves of the GPU
