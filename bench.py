@@ -200,10 +200,30 @@ def secondary(args, dev, plan, inst, stream, flush):
     r1 = torch.empty(1, dtype=torch.float64, device=dev)
     lat = {}
     for path in ("fast", "conv", "hybrid"):
-        v = sorted(_events_ms(lambda: p1.omp_into(y1, c1["K"], x1, s1, t1, r1, path=path), 200, 10, stream))
-        lat[path] = {"p50_us": 1e3 * statistics.median(v), "p99_us": 1e3 * v[int(0.99 * (len(v) - 1))]}
-    out["omp_wht_fp64_single_latency"] = {"config": "partial WHT FP64, N=1024, M=256, K=16, noiseless, 1 instance",
-                                          **lat}
+        # one solve captured in a CUDA graph, replayed 10^4 times, each
+        # replay timed with CUDA events on the replay stream
+        gs = torch.cuda.Stream()
+        with torch.cuda.stream(gs):
+            for _ in range(3):
+                p1.omp_into(y1, c1["K"], x1, s1, t1, r1, path=path)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            p1.omp_into(y1, c1["K"], x1, s1, t1, r1, path=path)
+        torch.cuda.synchronize()
+        n_rep = 10000
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_rep)]
+        with torch.cuda.stream(gs):
+            for e0, e1 in ev:
+                e0.record(gs)
+                graph.replay()
+                e1.record(gs)
+        torch.cuda.synchronize()
+        v = sorted(1e3 * a.elapsed_time(b) for a, b in ev)
+        lat[path] = {"p50_us": statistics.median(v), "p99_us": v[int(0.99 * (len(v) - 1))], "repeats": n_rep}
+        assert int(t1.item()) > 0
+    out["omp_wht_fp64_single_latency"] = {"config": "partial WHT FP64, N=1024, M=256, K=16, noiseless, 1 instance; "
+                                                    "one solve in a CUDA graph, 10^4 replays", **lat}
 
     rng_inst = synth.make_batch("dft", 8192, 64, 4, 256, snr_db=None, prec="fp32", seed=3)
     p3 = binding.Plan(8192, rng_inst["omega"], "dft", "fp32")
