@@ -416,9 +416,16 @@ extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, in
   cudaStream_t st = (cudaStream_t)stream;
 
   int err = 0, grid = 0;
+  // a few instances: one cluster of CTAs per instance (same results as the
+  // persistent kernel, spread over more SMs)
+  const bool cluster = !plan->v.large && batch <= kClusterMaxBatch && K <= kClusterMaxK &&
+                       omp_cluster_smem(plan->v, K, h.path) <= (size_t)200 * 1024;
   if (plan->v.large) {
     if (batch > kMaxLargeBatch) return CS_ERR_UNSUPPORTED;
     const cs_status r = ensure_ws(plan, large_omp_ws(plan->v, K, h.path, batch), st);
+    if (r != CS_OK) return r;
+  } else if (cluster) {
+    const cs_status r = ensure_ws(plan, omp_cluster_workspace_bytes(plan->v, K, batch), st);
     if (r != CS_OK) return r;
   } else {
     grid = omp_grid(plan->v, K, h.path, batch, &err);
@@ -438,6 +445,7 @@ extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, in
   a.iters_out = iters_dev;
   a.res_out = resnorm_dev;
   if (plan->v.large) CS_CUDA(large_omp(plan->v, a, plan->ws, st), "omp kernels");
+  else if (cluster) CS_CUDA(launch_omp_cluster(plan->v, a, plan->ws, st), "omp cluster kernel");
   else CS_CUDA(launch_omp(plan->v, a, plan->ws, grid, st), "omp kernel");
   return CS_OK;
 }

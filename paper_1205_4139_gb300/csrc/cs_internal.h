@@ -93,6 +93,13 @@ int omp_grid(const PlanView& P, int K, int path, int64_t batch, int* err);
 size_t omp_workspace_bytes(const PlanView& P, int K, int grid);
 cudaError_t launch_omp(const PlanView& P, const OmpLaunch& a, void* ws, int grid, cudaStream_t st);
 
+// OMP on small batches, one cluster of CTAs per instance (cs_omp_cluster.cu)
+constexpr int kClusterMaxBatch = 19;  // up to 152 CTAs: one wave of 8-CTA clusters
+constexpr int kClusterMaxK = 256;     // every CTA keeps its own FP64 factor
+size_t omp_cluster_smem(const PlanView& P, int K, int path);
+size_t omp_cluster_workspace_bytes(const PlanView& P, int K, int64_t batch);
+cudaError_t launch_omp_cluster(const PlanView& P, const OmpLaunch& a, void* ws, cudaStream_t st);
+
 // large plans (cs_large.cu)
 cudaError_t large_tables(const PlanView& P, void* lt64, void* lt32, cudaStream_t st);
 cudaError_t large_kernel_vector(const PlanView& P, void* c64_full, void* tmp, cudaStream_t st);
