@@ -163,7 +163,8 @@ cs_status cs_correlate_fast(cs_plan_t plan, const void* h0_dev, const int32_t* s
  *              downdate ||r_t||^2 = ||y||^2 - sum |z_k|^2 of the Cholesky
  *              update
  * Any output pointer except supp_dev may be NULL (supp_dev too when K = 0).  halt may be NULL
- * (rel_tol 1e-6, hybrid path, default switch).  Limits: 0 <= K <= min(M, 1024). */
+ * (rel_tol 1e-6, hybrid path, default switch).  Limits: 0 <= K <= min(M, 1024)
+ * for N <= 8192, 0 <= K <= min(M, 4096) for larger plans. */
 cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
                  void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev,
                  void* stream);

@@ -384,7 +384,7 @@ extern "C" cs_status cs_correlate_fast(cs_plan_t plan, const void* h0_dev, const
   if (!plan || batch < 0 || s < 0 || s > plan->v.N) return CS_ERR_INVALID;
   if (batch > 0 && !h0_dev) return CS_ERR_INVALID;
   if (batch > 0 && s > 0 && (!supp_dev || !x_dev)) return CS_ERR_INVALID;
-  if (s > kMaxK) return CS_ERR_UNSUPPORTED;
+  if (s > (plan->v.large ? kMaxKLarge : kMaxK)) return CS_ERR_UNSUPPORTED;
   if (batch == 0 || (!h_dev && !argmax_dev)) return CS_OK;
   if (plan->v.large) {
     if (batch > kMaxLargeBatch) return CS_ERR_UNSUPPORTED;
@@ -404,7 +404,7 @@ extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, in
                             void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev, void* stream) {
   if (!plan || batch < 0 || K < 0) return CS_ERR_INVALID;
   if (K > plan->v.M) return CS_ERR_INVALID;
-  if (K > kMaxK) return CS_ERR_UNSUPPORTED;
+  if (K > (plan->v.large ? kMaxKLarge : kMaxK)) return CS_ERR_UNSUPPORTED;
   cs_halt h = {1e-6, CS_PATH_HYBRID, -1, 0};
   if (halt) h = *halt;
   if (!(h.rel_tol >= 0.0) || !std::isfinite(h.rel_tol)) return CS_ERR_INVALID;

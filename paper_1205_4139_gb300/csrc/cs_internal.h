@@ -10,6 +10,7 @@ constexpr int kThreads = 256;
 constexpr int kMaxLogN = 13;       // N <= 8192: one instance per CTA
 constexpr int kMaxLogNLarge = 24;  // four-step transforms through global memory
 constexpr int kMaxK = 1024;
+constexpr int kMaxKLarge = 4096;       // large plans: the factor lives in global memory
 constexpr int kMaxLargeBatch = 65535;  // large plans: instances per call
 
 // Type-erased view of a plan's device tables.

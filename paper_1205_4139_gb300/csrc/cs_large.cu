@@ -999,6 +999,8 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
   if (Z && (e = cudaMemsetAsync(Z, 0, Nv, s)) != cudaSuccess) return e;
   if (A.xz && (e = cudaMemsetAsync(A.xz, 0, Nv, s)) != cudaSuccess) return e;
   const size_t ls_smem = (size_t)(a.K > 0 ? a.K : 1) * sizeof(W);
+  if ((e = allow_smem(lls_one_kernel<E>, ls_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(lls_u_kernel<E>, ls_smem)) != cudaSuccess) return e;
   const double isq = inv_sqrt_n(P.logN);
   const int rp = row_parts(P), fp = fast_parts(P);
   const int T_end = a.K > 0 ? a.K : 1;

@@ -208,7 +208,7 @@ cs_status check_request(const cs_request* q) {
   if (q->N > (int64_t(1) << kMaxLogNLarge)) return CS_ERR_UNSUPPORTED;
   if (q->algo == CS_ALGO_OMP) {
     if (q->K < 0 || q->K > q->M) return CS_ERR_INVALID;
-    if (q->K > kMaxK) return CS_ERR_UNSUPPORTED;
+    if (q->K > (q->N > (int64_t(1) << kMaxLogN) ? kMaxKLarge : kMaxK)) return CS_ERR_UNSUPPORTED;
   } else if (q->algo == CS_ALGO_COSAMP || q->algo == CS_ALGO_SP) {
     if (q->K < 1 || (q->algo == CS_ALGO_SP ? 2 : 3) * (int64_t)q->K > q->M) return CS_ERR_INVALID;
     if (q->K > 128 || q->N > (int64_t(1) << kMaxLogN)) return CS_ERR_UNSUPPORTED;

@@ -203,3 +203,25 @@ def test_large_big_dft_sampled():
     upto = next((t for t, g in enumerate(ref["gap"]) if g <= 1e-3), len(ref["gap"]))
     assert supp.cpu().numpy()[0][:upto].tolist() == ref["support"][:upto]
     assert plan.device_error() == 0
+
+
+def test_large_K_beyond_1024_properties():
+    """K above the one-CTA limit on a large plan (factor in global memory):
+    checked by what holds at any size: K columns selected, all distinct; the
+    final residual r = y - Phi_Lambda x is orthogonal to the chosen columns
+    (least-squares optimality, step 6) and its norm is the reported one."""
+    N, M, K = 1 << 14, 4096, 1100
+    inst = synth.make_batch("dft", N, M, K, 1, snr_db=30, prec="fp64", seed=77)
+    plan = binding.Plan(N, inst["omega"], "dft", "fp64")
+    x, supp, it, rn = plan.omp(torch.from_numpy(inst["Y"]).cuda(), K, path="hybrid", t_switch=16)
+    torch.cuda.synchronize()
+    assert plan.device_error() == 0
+    it = int(it.item())
+    s = supp.cpu().numpy()[0][:it]
+    xv = x.cpu().numpy()[0][:it]
+    assert it == K and len(set(s.tolist())) == K
+    y = inst["Y"][0].astype(np.complex128)
+    r = y - tro.synthesize("dft", N, inst["omega"], s, xv)
+    h = tro.correlate("dft", N, inst["omega"], r)
+    assert np.max(np.abs(h[s])) < 1e-8 * np.linalg.norm(y)
+    assert abs(float(rn.item()) - np.linalg.norm(r) / np.linalg.norm(y)) < 1e-6
