@@ -69,9 +69,10 @@ typedef enum { CS_PATH_FAST = 0, CS_PATH_CONV = 1, CS_PATH_HYBRID = 2 } cs_path;
  * the tolerance).  A zero measurement halts before the first iteration; a
  * selected column whose Cholesky pivot is <= 1e-10 * M/N (numerically
  * dependent on the support) ends the run without being added.
- * t_switch < 0 selects the plan's switch point: the one cs_plan_tune
- * measured, if it has run on this plan, else the flop-model default
- * (cs_plan_info).
+ * t_switch < 0 selects the plan's switch point (cs_plan_switch): the one
+ * cs_plan_tune measured, if it has run on this plan, else a crossover table
+ * measured on GB300 by log2 N (the flop-model point of cs_plan_info is far
+ * lower than the measured crossovers).
  * max_iter bounds the iterations of cs_sp / cs_cosamp (<= 0: K for SP, 50 for
  * CoSaMP); cs_omp ignores it (its bound is K). */
 typedef struct {
@@ -123,6 +124,11 @@ cs_status cs_plan_destroy(cs_plan_t plan);
  * NULL. */
 cs_status cs_plan_info(cs_plan_t plan, int64_t* N, int64_t* M, int32_t* kind, int32_t* prec,
                        int32_t* t_switch_default);
+
+/* The switch point calls with t_switch < 0 use: cs_plan_tune's, if it has
+ * run on this plan, else the GB300 crossover for the plan's N (64 for
+ * N <= 8192; 80 to 160 for larger N). */
+cs_status cs_plan_switch(cs_plan_t plan, int32_t* t_switch);
 
 /* Errors the kernels detected on the device since the last call (0 = none;
  * bit 0: an OMP launch stopped because its phase loop reached its bound,

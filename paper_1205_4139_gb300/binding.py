@@ -22,7 +22,7 @@ KINDS = {"wht": CS_WHT, "dft": CS_DFT}
 PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 
 # Every function include/csfast.h declares.
-EXPORTS = ["cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
+EXPORTS = ["cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_switch", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
            "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
            "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy",
            "cs_admit_next", "cs_status_string", "cs_last_error"]
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH):
     L.cs_plan_create.argtypes = [i64, pi32, i64, i32, i32, vp, ctypes.POINTER(vp)]
     L.cs_plan_create_ex.argtypes = [i64, pi32, i64, i32, i32, ctypes.c_uint32, vp, ctypes.POINTER(vp)]
     L.cs_plan_memory.argtypes = [vp, pi64]
+    L.cs_plan_switch.argtypes = [vp, pi32]
     L.cs_plan_destroy.argtypes = [vp]
     L.cs_plan_info.argtypes = [vp, pi64, pi64, pi32, pi32, pi32]
     L.cs_plan_kernel.argtypes = [vp, vp, i32, vp]
@@ -89,7 +90,7 @@ def load(path: str = LIB_PATH):
     L.cs_server_destroy.argtypes = [vp]
     L.cs_admit_next.argtypes = [pi64, pi32, i32, i64, i64, i32]
     L.cs_admit_next.restype = ctypes.c_int32
-    for f in ("cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
+    for f in ("cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_switch", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
               "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
               "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy"):
         getattr(L, f).restype = ctypes.c_int
@@ -161,6 +162,12 @@ class Plan:
         _check(load().cs_plan_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(k), ctypes.byref(p),
                                    ctypes.byref(ts)))
         return {"N": n.value, "M": m.value, "kind": k.value, "prec": p.value, "t_switch_default": ts.value}
+
+    def switch_point(self) -> int:
+        """The switch point used when t_switch < 0 (cs_plan_switch)."""
+        t = ctypes.c_int32()
+        _check(load().cs_plan_switch(self._h, ctypes.byref(t)))
+        return t.value
 
     def memory(self) -> int:
         """Device bytes of the plan's tables (cs_plan_memory)."""

@@ -86,9 +86,25 @@ int plan_t_switch_default(cs_plan_t plan) { return plan->t_switch_default; }
 void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 }  // namespace csf
 
-// Switch point used when a call passes t_switch < 0: the measured one once
-// cs_plan_tune has run, else the flop-model default.
-static int plan_switch(const cs_plan_s* p) { return p->t_switch_tuned >= 0 ? p->t_switch_tuned : p->t_switch_default; }
+// Crossover of the two correlations measured on GB300 (python -m
+// paper_1205_4139_gb300.switch_curves: OMP per-iteration cost of kernel sums
+// and of transforms versus t, M = N/4, partial DFT and WHT): the t above
+// which transforms are cheaper per iteration, by log2 N.  One-CTA plans
+// (batches of instances in shared memory) cross near 64; large plans (one
+// instance spread over the GPU, least squares and launch latency shared by
+// both paths) between about 70 and 200.
+static int gb300_switch(int logN) {
+  if (logN <= kMaxLogN) return 64;
+  static const int table[] = {160, 112, 96, 80, 80, 80, 96, 112, 112, 112, 112};  // log2 N = 14 .. 24
+  const int i = logN - 14;
+  return table[i < 0 ? 0 : (i > 10 ? 10 : i)];
+}
+
+// Switch point used when a call passes t_switch < 0: the one cs_plan_tune
+// measured for this plan, else the GB300 crossover table.
+static int plan_switch(const cs_plan_s* p) {
+  return p->t_switch_tuned >= 0 ? p->t_switch_tuned : gb300_switch(p->v.logN);
+}
 
 static void plan_free(cs_plan_s* p) {
   if (!p) return;
@@ -575,5 +591,11 @@ extern "C" cs_status cs_plan_tune(cs_plan_t plan, const void* y_dev, int64_t bat
     ms_out[i] = ms[i];
   }
   if (n_out) *n_out = (int)ladder.size();
+  return CS_OK;
+}
+
+extern "C" cs_status cs_plan_switch(cs_plan_t plan, int32_t* t_switch) {
+  if (!plan || !t_switch) return CS_ERR_INVALID;
+  *t_switch = plan_switch(plan);
   return CS_OK;
 }

@@ -22,7 +22,9 @@ def test_tune_then_default_switch(kind, prec, N, M, K):
     inst = synth.make_batch(kind, N, M, K, 40, snr_db=None, dist="gauss", prec=prec, seed=7)
     plan = binding.Plan(N, inst["omega"], kind, prec)
     y = torch.from_numpy(inst["Y"]).cuda()
+    assert plan.switch_point() == 64  # the GB300 crossover of one-CTA plans, before tuning
     t_best, curve = plan.tune(y, K, rel_tol=1e-6)
+    assert plan.switch_point() == t_best
     assert t_best in curve and 1 in curve and K in curve
     assert plan.info()["t_switch_default"] in curve
     assert all(v > 0 for v in curve.values())
@@ -57,3 +59,9 @@ def test_tune_rejects_bad_arguments():
         plan.tune(y, 0)
     with pytest.raises(binding.CsError):
         plan.tune(y, 65)
+
+
+def test_untuned_large_plan_uses_measured_crossover():
+    om = synth.draw_omega(1 << 16, 8192, np.random.default_rng(2))
+    assert binding.Plan(1 << 16, om, "dft", "fp32").switch_point() == 96
+    assert binding.Plan(1 << 14, om[om < (1 << 14)], "wht", "fp32").switch_point() == 160
