@@ -36,8 +36,7 @@ namespace csf {
 namespace {
 
 constexpr int kLT = 256;                   // threads per CTA of every kernel here
-constexpr int kFastCH = 8;                 // outputs per thread of the fast correlation
-constexpr int kFastTile = kLT * kFastCH;   // outputs per CTA of the fast correlation
+constexpr int kFastMaxCH = 8;              // outputs per thread of the fast correlation, at most
 constexpr int kMaxBatchY = 65535;          // instances ride on gridDim.y
 constexpr int kU = 8;                      // independent accesses per thread in flight in the pass loops
 
@@ -366,11 +365,11 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
 }
 
 // ------------------------------------------------------ fast correlation
-// h(j) = h0(j) - sum_{k<s} x_k c(j (-) lam_k) for the kFastTile outputs of
+// h(j) = h0(j) - sum_{k<s} x_k c(j (-) lam_k) for the kLT * CH outputs of
 // this CTA (Eq. kernelsumOMP); lam / x of instance b start at b * kstride.
 // Stores h if h != NULL; the arg-max over j with a clear bit (all j if
 // bits == NULL) goes to the partial.
-template <class E, bool DFT, int CF>
+template <class E, bool DFT, int CF, int CH>
 __global__ void __launch_bounds__(kLT) lfast_kernel(LDev<E> P, const E* __restrict__ h0,
                                                     const int* __restrict__ lam, const E* __restrict__ xw, int s,
                                                     int64_t kstride, const uint32_t* __restrict__ bits,
@@ -391,17 +390,17 @@ __global__ void __launch_bounds__(kLT) lfast_kernel(LDev<E> P, const E* __restri
     xs[k] = xw[b * kstride + k];
   }
   __syncthreads();
-  const int j0 = blockIdx.x * kFastTile + threadIdx.x;
+  const int j0 = blockIdx.x * (kLT * CH) + threadIdx.x;
   const E* hb = h0 + b * (int64_t)N;
-  E acc[kFastCH];
+  E acc[CH];
 #pragma unroll
-  for (int e = 0; e < kFastCH; ++e) acc[e] = hb[j0 + e * kLT];
+  for (int e = 0; e < CH; ++e) acc[e] = hb[j0 + e * kLT];
 #pragma unroll 2
   for (int k = 0; k < s; ++k) {
     const int l = ls[k];
     const E xk = xs[k];
 #pragma unroll
-    for (int e = 0; e < kFastCH; ++e) {
+    for (int e = 0; e < CH; ++e) {
       const int j = j0 + e * kLT;
       const int d = DFT ? ((j - l) & (N - 1)) : (j ^ l);
       E cv;
@@ -416,7 +415,7 @@ __global__ void __launch_bounds__(kLT) lfast_kernel(LDev<E> P, const E* __restri
   V bv = (V)-1;
   int bj = 0x7fffffff;
 #pragma unroll
-  for (int e = 0; e < kFastCH; ++e) {
+  for (int e = 0; e < CH; ++e) {
     const int j = j0 + e * kLT;
     if (hout) hout[j] = acc[e];
     if (!bb || !in_bits(bb, j)) {
@@ -433,7 +432,7 @@ __global__ void __launch_bounds__(kLT) lfast_kernel(LDev<E> P, const E* __restri
 // arg-max of each instance's partials -> amax[b]
 template <class V>
 __global__ void __launch_bounds__(kLT) lreduce_kernel(const V* __restrict__ part_v, const int* __restrict__ part_j,
-                                                      int nparts, int32_t* __restrict__ amax) {
+                                                      int stride, int nparts, int32_t* __restrict__ amax) {
   __shared__ V rv[34];
   __shared__ int rj[34];
   __shared__ V ov;
@@ -442,8 +441,8 @@ __global__ void __launch_bounds__(kLT) lreduce_kernel(const V* __restrict__ part
   V bv = (V)-1;
   int bj = 0x7fffffff;
   for (int i = threadIdx.x; i < nparts; i += kLT) {
-    const V v = part_v[b * nparts + i];
-    const int j = part_j[b * nparts + i];
+    const V v = part_v[b * stride + i];
+    const int j = part_j[b * stride + i];
     if (v >= (V)0 && better(v, j, bv, bj)) {
       bv = v;
       bj = j;
@@ -704,23 +703,34 @@ __device__ void ls_w_phase(const LOmpArgs<E>& a, int G, int gi, int64_t b) {
   const W* u = a.u + b * K;
   const int* lam = a.lam + b * K;
   E* xz = a.xz ? a.xz + b * (int64_t)N : nullptr;
-  // w_k = -invd sum_{i=k}^{p-1} conj(u_i) B[i][k], one column per thread;
-  // a warp walks the rows in step from its first column so that its reads
-  // of row i are one contiguous segment
+  // w_k = -invd sum_{i=k}^{p-1} conj(u_i) B[i][k] over strips of 32 columns:
+  // the lanes of a warp take the strip's columns (one contiguous segment of
+  // each row), the 8 warps take every 8th row, and the 8 partial sums of a
+  // column are added in shared memory in a fixed order
+  constexpr int RG = kLT / 32;
+  __shared__ W wpart[RG][32];
+  const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
   const int k0 = col_cut(p, gi, G), k1 = col_cut(p, gi + 1, G);
-  for (int kw = k0 + (threadIdx.x & ~31); kw < k1; kw += kLT) {
-    const int k = kw + (threadIdx.x & 31);
-    if (k >= k1) continue;
+  for (int kw = k0; kw < k1; kw += 32) {
+    const int k = kw + lane;
     W acc = W{};
-    for (int i = kw; i < p; ++i)
-      if (i >= k) acc = fmacv(acc, u[i], B[pidx(i) + k]);
-    const W wk = scale(acc, -invd);
-    B[pidx(p) + k] = wk;
-    const W xk = fmacv(x[k], wk, zeta);
-    x[k] = xk;
-    const E e = from_w<E>(xk);
-    xw[k] = e;
-    if (xz) xz[lam[k]] = e;
+    if (k < k1)
+      for (int i = kw + rg; i < p; i += RG)
+        if (i >= k) acc = fmacv(acc, u[i], B[pidx(i) + k]);
+    wpart[rg][lane] = acc;
+    __syncthreads();
+    if (rg == 0 && k < k1) {
+      W sum = wpart[0][lane];
+      for (int r = 1; r < RG; ++r) sum = add(sum, wpart[r][lane]);
+      const W wk = scale(sum, -invd);
+      B[pidx(p) + k] = wk;
+      const W xk = fmacv(x[k], wk, zeta);
+      x[k] = xk;
+      const E e = from_w<E>(xk);
+      xw[k] = e;
+      if (xz) xz[lam[k]] = e;
+    }
+    __syncthreads();
   }
   if (gi == 0 && threadIdx.x == 0) {
     B[pidx(p) + p] = make_w<W>(invd, 0.0);
@@ -773,11 +783,12 @@ __global__ void __launch_bounds__(kLT) lls_one_kernel(LOmpArgs<E> a, int nparts)
   ls_w_phase(a, 1, 0, (int64_t)blockIdx.y);
 }
 
-// CTAs per instance for the least squares at p columns: about 8192 complex
-// FP64 multiply-adds each, at most gmax
+// CTAs per instance for the least squares at p columns: about 1024 complex
+// FP64 multiply-adds each (a few microseconds of one SM's FP64 pipe), at most
+// gmax
 inline int ls_ctas(int p, int gmax) {
   const int64_t work = (int64_t)p * (p + 1) / 2;
-  int64_t g = (work + 8191) / 8192;
+  int64_t g = (work + 1023) / 1024;
   if (g < 1) g = 1;
   return (int)(g < gmax ? g : gmax);
 }
@@ -813,35 +824,65 @@ cudaError_t run_row(const LDev<E>& P, const E* T, int neg, double scl, E* out, c
   return cudaGetLastError();
 }
 
+// Outputs per thread of the kernel sums: the most (up to 8) that still give
+// about two CTAs per SM over the batch (small N needs small tiles to use the
+// GPU; large N needs several outputs per thread to keep loads in flight).
+inline int fast_ch(int N, int64_t batch) {
+  for (int ch = kFastMaxCH; ch > 1; ch >>= 1)
+    if ((int64_t)(N / (kLT * ch)) * batch >= 2 * 152) return ch;
+  return 1;
+}
+
+template <class E, bool DFT, int CF, int CH>
+cudaError_t run_fast_t(const LDev<E>& P, const E* h0, const int* lam, const E* xw, int s, int64_t kstride,
+                       const uint32_t* bits, E* h, typename NormT<E>::V* pv, int* pj, int nparts, const LState* st,
+                       int64_t batch, size_t smem, cudaStream_t strm) {
+  const cudaError_t e = allow_smem(lfast_kernel<E, DFT, CF, CH>, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(P.N / (kLT * CH), (unsigned)batch);
+  lfast_kernel<E, DFT, CF, CH><<<grid, kLT, smem, strm>>>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st);
+  return cudaGetLastError();
+}
+
+template <class E, bool DFT, int CF>
+cudaError_t run_fast_cf(const LDev<E>& P, const E* h0, const int* lam, const E* xw, int s, int64_t kstride,
+                        const uint32_t* bits, E* h, typename NormT<E>::V* pv, int* pj, int nparts, const LState* st,
+                        int64_t batch, size_t smem, int ch, cudaStream_t strm) {
+  switch (ch) {
+    case 8: return run_fast_t<E, DFT, CF, 8>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st, batch, smem, strm);
+    case 4: return run_fast_t<E, DFT, CF, 4>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st, batch, smem, strm);
+    case 2: return run_fast_t<E, DFT, CF, 2>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st, batch, smem, strm);
+    default: return run_fast_t<E, DFT, CF, 1>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st, batch, smem, strm);
+  }
+}
+
+// Launches the kernel sums; *np receives the number of arg-max partials per
+// instance (one per CTA).
 template <class E, bool DFT>
 cudaError_t run_fast(const LDev<E>& P, const E* h0, const int* lam, const E* xw, int s, int64_t kstride,
                      const uint32_t* bits, E* h, typename NormT<E>::V* pv, int* pj, int nparts, const LState* st,
-                     int64_t batch, cudaStream_t strm) {
+                     int64_t batch, cudaStream_t strm, int* np = nullptr) {
   using V = typename NormT<E>::V;
   const size_t smem = al16((size_t)s * sizeof(E)) + al16((size_t)s * sizeof(int)) + al16(34 * sizeof(V)) +
                       34 * sizeof(int);
-  const dim3 grid(P.N / kFastTile, (unsigned)batch);
-  cudaError_t e;
-  if (DFT && P.cfmt == CFMT_HALF) {
-    if ((e = allow_smem(lfast_kernel<E, DFT, CFMT_HALF>, smem)) != cudaSuccess) return e;
-    lfast_kernel<E, DFT, CFMT_HALF><<<grid, kLT, smem, strm>>>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts,
-                                                               st);
-  } else if (!DFT && P.cfmt == CFMT_INT) {
-    if ((e = allow_smem(lfast_kernel<E, DFT, CFMT_INT>, smem)) != cudaSuccess) return e;
-    lfast_kernel<E, DFT, CFMT_INT><<<grid, kLT, smem, strm>>>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts,
-                                                              st);
-  } else {
-    if ((e = allow_smem(lfast_kernel<E, DFT, CFMT_FULL>, smem)) != cudaSuccess) return e;
-    lfast_kernel<E, DFT, CFMT_FULL><<<grid, kLT, smem, strm>>>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts,
-                                                               st);
-  }
-  return cudaGetLastError();
+  const int ch = fast_ch(P.N, batch);
+  if (np) *np = P.N / (kLT * ch);
+  if (DFT && P.cfmt == CFMT_HALF)
+    return run_fast_cf<E, DFT, CFMT_HALF>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st, batch, smem, ch,
+                                          strm);
+  if (!DFT && P.cfmt == CFMT_INT)
+    return run_fast_cf<E, DFT, CFMT_INT>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st, batch, smem, ch,
+                                         strm);
+  return run_fast_cf<E, DFT, CFMT_FULL>(P, h0, lam, xw, s, kstride, bits, h, pv, pj, nparts, st, batch, smem, ch,
+                                        strm);
 }
 
 template <class E>
 int row_parts(const LDev<E>& P) { return (1 << P.n1) / tile_c<E>(); }
+// arg-max partials per instance the kernel sums can leave (one per CTA, at
+// the smallest tile)
 template <class E>
-int fast_parts(const LDev<E>& P) { return P.N / kFastTile; }
+int fast_parts(const LDev<E>& P) { return P.N / kLT; }
 
 inline double inv_sqrt_n(int logN) { return 1.0 / std::sqrt(std::ldexp(1.0, logN)); }
 
@@ -871,7 +912,7 @@ cudaError_t corr_t(const PlanView& Pv, const void* r, int64_t batch, void* h, in
   e = run_row<E, DFT, SK_H>(P, T, DFT, inv_sqrt_n(P.logN), (E*)h, nullptr, nullptr, amax ? pv : nullptr,
                             amax ? pj : nullptr, np, nullptr, batch, s);
   if (e != cudaSuccess || !amax) return e;
-  lreduce_kernel<V><<<(unsigned)batch, kLT, 0, s>>>(pv, pj, np, amax);
+  lreduce_kernel<V><<<(unsigned)batch, kLT, 0, s>>>(pv, pj, np, np, amax);
   return cudaGetLastError();
 }
 
@@ -901,10 +942,11 @@ cudaError_t fast_t(const PlanView& Pv, const void* h0, const int32_t* supp, cons
     lbits_kernel<<<(unsigned)batch, kLT, 0, st>>>(supp, s, P.N, bits);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  int used = np;
   e = run_fast<E, DFT>(P, (const E*)h0, supp, (const E*)x, s, s, bits, (E*)h, amax ? pv : nullptr,
-                       amax ? pj : nullptr, np, nullptr, batch, st);
+                       amax ? pj : nullptr, np, nullptr, batch, st, &used);
   if (e != cudaSuccess || !amax) return e;
-  lreduce_kernel<V><<<(unsigned)batch, kLT, 0, st>>>(pv, pj, np, amax);
+  lreduce_kernel<V><<<(unsigned)batch, kLT, 0, st>>>(pv, pj, np, used, amax);
   return cudaGetLastError();
 }
 
@@ -1002,7 +1044,7 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
   if ((e = allow_smem(lls_one_kernel<E>, ls_smem)) != cudaSuccess) return e;
   if ((e = allow_smem(lls_u_kernel<E>, ls_smem)) != cudaSuccess) return e;
   const double isq = inv_sqrt_n(P.logN);
-  const int rp = row_parts(P), fp = fast_parts(P);
+  const int rp = row_parts(P);
   const int T_end = a.K > 0 ? a.K : 1;
   for (int t = 1; t <= T_end; ++t) {
     int np;
@@ -1016,9 +1058,8 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
       np = rp;
     } else if (a.path == 0 || (a.path == 2 && t <= a.t_switch)) {  // kernel sums over t - 1 atoms
       if ((e = run_fast<E, DFT>(P, A.h0, A.lam, A.xw, t - 1, a.K, A.bits, nullptr, A.part_v, A.part_j, L.nparts,
-                                A.st, batch, s)) != cudaSuccess)
+                                A.st, batch, s, &np)) != cudaSuccess)
         return e;
-      np = fp;
     } else {  // r = y - Phi x by a forward transform of zf(x), then h = A^H zf(r)
       if ((e = run_col<E, DFT, LD_DENSE>(P, A.xz, P.N, T, A.st, batch, s)) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s)) !=
