@@ -783,12 +783,12 @@ __global__ void __launch_bounds__(kLT) lls_one_kernel(LOmpArgs<E> a, int nparts)
   ls_w_phase(a, 1, 0, (int64_t)blockIdx.y);
 }
 
-// CTAs per instance for the least squares at p columns: about 1024 complex
+// CTAs per instance for the least squares at p columns: about 2048 complex
 // FP64 multiply-adds each (a few microseconds of one SM's FP64 pipe), at most
 // gmax
 inline int ls_ctas(int p, int gmax) {
   const int64_t work = (int64_t)p * (p + 1) / 2;
-  int64_t g = (work + 1023) / 1024;
+  int64_t g = (work + 2047) / 2048;
   if (g < 1) g = 1;
   return (int)(g < gmax ? g : gmax);
 }
@@ -988,8 +988,10 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
     L.nyp = (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
   }
   L.yp = o;   o = al16(o + (size_t)batch * L.nyp * sizeof(double));
-  {  // CTAs per instance for the least squares: fill about 4 waves of the GPU
-    int64_t g = (4 * 152 + batch - 1) / batch;
+  {  // CTAs per instance for the least squares: about two per SM over the
+     // batch (more only adds per-CTA overhead, and concurrent calls from the
+     // request runtime share the GPU)
+    int64_t g = (2 * 152 + batch - 1) / batch;
     L.gmax = (int)(g < 1 ? 1 : (g > 256 ? 256 : g));
   }
   L.tm = o;   o = al16(o + (size_t)batch * L.gmax * 3 * sizeof(double));
