@@ -247,6 +247,15 @@ template <class V>
 __device__ __forceinline__ bool better(V av, int aj, V bv, int bj) {
   return av > bv || (av == bv && aj < bj);
 }
+// FP64 magnitudes compare as signed 64-bit integers: the bit pattern of a
+// non-negative double orders like the double, and the negative sentinel
+// (sign bit set) is below every one of them.  Integer compares run on the
+// ALU pipe, FP64 compares on GB300's narrow FP64 pipe.
+template <>
+__device__ __forceinline__ bool better<double>(double av, int aj, double bv, int bj) {
+  const long long a = __double_as_longlong(av), b = __double_as_longlong(bv);
+  return a > b || (a == b && aj < bj);
+}
 
 template <class V>
 __device__ __forceinline__ void warp_argmax(V& v, int& j) {
