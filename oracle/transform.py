@@ -14,7 +14,9 @@ matrix, fwht being the radix-2 butterflies written out below.  The least
 squares of step 6 forms Phi_t from the closed-form entries of its columns and
 calls the dense oracle's Cholesky solve; identification and halting are the
 dense oracle's (oracle.omp), so the two differ only in how Phi is applied.
-Tests pin this module against the dense oracle at N <= 4096.
+Subspace pursuit and CoSaMP follow oracle.pursuits step for step with the
+same substitution.  Tests pin this module against the dense oracle at
+N <= 4096.
 """
 from __future__ import annotations
 
@@ -134,4 +136,80 @@ def omp(kind: str, N: int, omega, y, K: int, rel_tol: float = 1e-6, dep_tol: flo
     out["support"] = lam
     out["x"] = x
     out["iters"] = len(lam)
+    return out
+
+
+def _ls_cols(kind, N, omega, y, cols):
+    """Least squares on the columns `cols` (the dense oracle's Cholesky solve on
+    the closed-form columns)."""
+    from .pursuits import ls
+    cols = np.asarray(cols, dtype=np.int64)
+    if len(cols) == 0:
+        return np.zeros(0, dtype=y.dtype)
+    return ls(columns(kind, N, omega, cols), y, np.arange(len(cols)))
+
+
+def subspace_pursuit(kind: str, N: int, omega, y, K: int, max_iter: int | None = None,
+                     rel_tol: float = 1e-6) -> dict:
+    """oracle.pursuits.subspace_pursuit with Phi applied through transforms
+    (same steps, same readings), for N too large for a dense Phi."""
+    from .pursuits import top_k
+    omega = np.asarray(omega, dtype=np.int64)
+    y = np.asarray(y).astype(np.complex128 if kind == "dft" or np.iscomplexobj(y) else np.float64)
+    ynorm = float(np.linalg.norm(y))
+    max_iter = K if max_iter is None else max_iter
+    out = {"support": np.zeros(0, np.int64), "x": np.zeros(0, y.dtype), "iters": 0, "resnorm": [ynorm],
+           "ynorm": ynorm}
+    if ynorm == 0.0 or K <= 0:
+        return out
+    res = lambda cols, x: y - synthesize(kind, N, omega, cols, x) if len(cols) else y
+    T = top_k(correlate(kind, N, omega, y), K)
+    x = _ls_cols(kind, N, omega, y, T)
+    rn = float(np.linalg.norm(res(T, x)))
+    out["resnorm"] = [rn]
+    it = 0
+    while it < max_iter and rn >= rel_tol * ynorm:
+        h = correlate(kind, N, omega, res(T, x))
+        Tp = np.union1d(T, top_k(h, K, excluded=T))
+        b = _ls_cols(kind, N, omega, y, Tp)
+        Tn = np.sort(Tp[top_k(b, K)])
+        xn = _ls_cols(kind, N, omega, y, Tn)
+        rn_new = float(np.linalg.norm(res(Tn, xn)))
+        it += 1
+        if rn_new >= rn:
+            break
+        T, x, rn = Tn, xn, rn_new
+        out["resnorm"].append(rn)
+    out.update(support=T, x=x, iters=it)
+    return out
+
+
+def cosamp(kind: str, N: int, omega, y, K: int, max_iter: int = 50, rel_tol: float = 1e-6) -> dict:
+    """oracle.pursuits.cosamp with Phi applied through transforms."""
+    from .pursuits import top_k
+    omega = np.asarray(omega, dtype=np.int64)
+    y = np.asarray(y).astype(np.complex128 if kind == "dft" or np.iscomplexobj(y) else np.float64)
+    ynorm = float(np.linalg.norm(y))
+    out = {"support": np.zeros(0, np.int64), "x": np.zeros(0, y.dtype), "iters": 0, "resnorm": [ynorm],
+           "ynorm": ynorm}
+    if ynorm == 0.0 or K <= 0:
+        return out
+    res = lambda cols, x: y - synthesize(kind, N, omega, cols, x) if len(cols) else y
+    S = np.zeros(0, np.int64)
+    x = np.zeros(0, y.dtype)
+    rn = ynorm
+    it = 0
+    while it < max_iter and rn >= rel_tol * ynorm:
+        h = correlate(kind, N, omega, res(S, x))
+        T = np.union1d(top_k(h, 2 * K), S)
+        b = _ls_cols(kind, N, omega, y, T)
+        keep = top_k(b, K)
+        Sn, xn = T[keep], b[keep]
+        rn_new = float(np.linalg.norm(res(Sn, xn)))
+        it += 1
+        if rn_new >= rn:
+            break
+        S, x, rn = Sn, xn, rn_new
+        out["resnorm"].append(rn)
+    out.update(support=S, x=x, iters=it)
     return out

@@ -87,3 +87,34 @@ def test_omp_large_noiseless_recovery(kind):
     r = inst["Y"][0] - tro.synthesize(kind, N, inst["omega"], t["support"], t["x"])
     h = tro.correlate(kind, N, inst["omega"], r)
     assert np.max(np.abs(h[t["support"]])) < 1e-10
+
+
+@pytest.mark.parametrize("kind", MODES)
+@pytest.mark.parametrize("algo", ["sp", "cosamp"])
+@pytest.mark.parametrize("N,M,K,snr", [(512, 160, 8, None), (1024, 300, 12, 30)])
+def test_pursuits_match_dense_oracle(kind, algo, N, M, K, snr):
+    from oracle import pursuits
+    inst = synth.make_batch(kind, N, M, K, 2, snr_db=snr, prec="fp64", seed=N + K)
+    Phi = matrices.sensing(kind, N, inst["omega"])
+    for b in range(2):
+        y = inst["Y"][b]
+        if algo == "sp":
+            a = pursuits.subspace_pursuit(Phi, y, K)
+            t = tro.subspace_pursuit(kind, N, inst["omega"], y, K)
+        else:
+            a = pursuits.cosamp(Phi, y, K)
+            t = tro.cosamp(kind, N, inst["omega"], y, K)
+        assert t["iters"] == a["iters"]
+        assert list(t["support"]) == list(a["support"])
+        assert np.max(np.abs(np.asarray(t["x"]) - np.asarray(a["x"]))) < 1e-10
+        assert np.allclose(t["resnorm"], a["resnorm"], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", MODES)
+@pytest.mark.parametrize("algo", ["sp", "cosamp"])
+def test_large_pursuits_recover_noiseless(kind, algo):
+    N, M, K = 1 << 14, 2048, 16
+    inst = synth.make_batch(kind, N, M, K, 1, snr_db=None, prec="fp64", seed=31)
+    f = tro.subspace_pursuit if algo == "sp" else tro.cosamp
+    r = f(kind, N, inst["omega"], inst["Y"][0], K)
+    assert sorted(r["support"].tolist()) == sorted(inst["support"][0].tolist())
