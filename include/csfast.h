@@ -90,8 +90,8 @@ typedef struct {
  * 0 <= M <= N.  Plans with N <= 8192 keep a whole instance on one SM (one
  * fused kernel per call); larger plans spread each instance over the GPU
  * with four-step transforms through global memory and queue a short
- * sequence of kernels per OMP iteration (at most 65535 instances per call;
- * cs_sp, cs_cosamp and cs_omp_noalloc return CS_ERR_UNSUPPORTED for them). */
+ * sequence of kernels per iteration (at most 65535 instances per call;
+ * cs_omp_noalloc returns CS_ERR_UNSUPPORTED for them). */
 cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind,
                          int32_t prec, void* stream, cs_plan_t* out);
 
@@ -193,6 +193,8 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
  * factor from c).  Outputs per instance: x_dev FP64 [K] and supp_dev [K] on
  * the final support in ascending column order (-1 / 0 past its size),
  * iters_dev (iterations run), resnorm_dev (||r|| / ||y||).
+ * Large plans (N > 8192) run the same steps with the correlation over the
+ * whole GPU and the top-k over N in two stages (per tile, then per instance).
  * Limits: 1 <= K, 2K <= M (SP), 3K <= M (CoSaMP), K <= 128. */
 cs_status cs_sp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
                 void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev, void* stream);

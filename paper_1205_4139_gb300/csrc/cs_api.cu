@@ -317,6 +317,7 @@ size_t solve_footprint(int64_t N, int64_t M, int32_t kind, int32_t prec, int32_t
   if (v.large) b += (size_t)N * wb;  // kernel-vector scratch while the plan is built
   size_t ws = 0;
   if (algo == 0) ws = v.large ? large_omp_ws(v, K, CS_PATH_HYBRID, 1) : omp_workspace_bytes(v, K, 1);
+  else if (v.large) ws = large_pursuit_ws(v, K, algo == 2 ? 0 : 1, 0, 1);
   else ws = pursuit_workspace_bytes(v, K, algo == 2 ? 0 : 1, 1);
   b += ws + (size_t)M * eb + (size_t)K * (wb + 4) + 64;
   return b;
@@ -471,7 +472,8 @@ static cs_status pursuit_call(int algo, cs_plan_t plan, const void* y_dev, int64
                               double* resnorm_dev, void* stream) {
   if (!plan || batch < 0 || K < 1) return CS_ERR_INVALID;
   if ((algo == 0 ? 2 : 3) * (int64_t)K > plan->v.M) return CS_ERR_INVALID;
-  if (K > 128 || plan->v.large) return CS_ERR_UNSUPPORTED;
+  if (K > 128) return CS_ERR_UNSUPPORTED;
+  if (plan->v.large && batch > kMaxLargeBatch) return CS_ERR_UNSUPPORTED;
   cs_halt h = {1e-6, CS_PATH_HYBRID, -1, 0};
   if (halt) h = *halt;
   if (!(h.rel_tol >= 0.0) || !std::isfinite(h.rel_tol)) return CS_ERR_INVALID;
@@ -481,11 +483,16 @@ static cs_status pursuit_call(int algo, cs_plan_t plan, const void* y_dev, int64
   const int t_switch = h.t_switch >= 0 ? h.t_switch : plan_switch(plan);
   const int fast = h.path == CS_PATH_FAST || (h.path == CS_PATH_HYBRID && K <= t_switch);
   cudaStream_t st = (cudaStream_t)stream;
-  int err = 0;
-  const int grid = pursuit_grid(plan->v, K, algo, fast, batch, &err);
-  if (err) return cuda_fail((cudaError_t)err, "pursuit configuration");
-  const cs_status r = ensure_ws(plan, pursuit_workspace_bytes(plan->v, K, algo, grid), st);
-  if (r != CS_OK) return r;
+  int err = 0, grid = 0;
+  if (plan->v.large) {
+    const cs_status r = ensure_ws(plan, large_pursuit_ws(plan->v, K, algo, fast, batch), st);
+    if (r != CS_OK) return r;
+  } else {
+    grid = pursuit_grid(plan->v, K, algo, fast, batch, &err);
+    if (err) return cuda_fail((cudaError_t)err, "pursuit configuration");
+    const cs_status r = ensure_ws(plan, pursuit_workspace_bytes(plan->v, K, algo, grid), st);
+    if (r != CS_OK) return r;
+  }
   PursuitLaunch a;
   a.y = y_dev;
   a.batch = batch;
@@ -498,7 +505,8 @@ static cs_status pursuit_call(int algo, cs_plan_t plan, const void* y_dev, int64
   a.supp_out = supp_dev;
   a.iters_out = iters_dev;
   a.res_out = resnorm_dev;
-  CS_CUDA(launch_pursuit(plan->v, a, plan->ws, grid, st), "pursuit kernel");
+  if (plan->v.large) CS_CUDA(large_pursuit(plan->v, a, plan->ws, st), "pursuit kernels");
+  else CS_CUDA(launch_pursuit(plan->v, a, plan->ws, grid, st), "pursuit kernel");
   return CS_OK;
 }
 

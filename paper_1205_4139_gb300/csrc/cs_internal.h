@@ -112,6 +112,8 @@ cudaError_t large_correlate_fast(const PlanView& P, const void* h0, const int32_
                                  int64_t batch, void* h, int32_t* amax, void* ws, cudaStream_t st);
 size_t large_omp_ws(const PlanView& P, int K, int path, int64_t batch);
 cudaError_t large_omp(const PlanView& P, const OmpLaunch& a, void* ws, cudaStream_t st);
+size_t large_pursuit_ws(const PlanView& P, int K, int algo, int fast, int64_t batch);
+cudaError_t large_pursuit(const PlanView& P, const PursuitLaunch& a, void* ws, cudaStream_t st);
 
 // subspace pursuit / CoSaMP
 int pursuit_grid(const PlanView& P, int K, int algo, int fast, int64_t batch, int* err);

@@ -30,6 +30,8 @@
 
 #include "cs_blocks.cuh"
 #include "cs_internal.h"
+#include "cs_ls.cuh"
+#include "cs_select.cuh"
 
 namespace csf {
 
@@ -1097,6 +1099,462 @@ cudaError_t kv_t(const PlanView& Pv, void* c64, void* tmp, cudaStream_t s) {
                                 nullptr, nullptr, 0, nullptr, 1, s);
 }
 
+// ------------------------------------------------------ SP and CoSaMP
+// The pursuits of cs_pursuit.cu on large plans.  Per iteration the host
+// queues: the correlation h over all N (kernel sums over the current support,
+// padded with zero coefficients, or the four-step passes of the residual),
+// the top-k selection (each tile of kLT * 8 outputs keeps its own top k, then
+// one CTA per instance takes the top k of the tiles' candidates: a tile's
+// (k+1)-th best can never be in the overall top k, and candidates are kept in
+// ascending j, so ties still go to the lower index), and the step: least
+// squares on the candidate set, pruning and the stop rules, one CTA per
+// instance, as in the one-CTA kernel.
+constexpr int kSelTile = kLT * 8;
+
+struct LPExtra {  // per instance, beside the LState done flag
+  int ns, m, it, pad;
+  double ynorm2, rn2, rn2_new, ls_rn2;
+};
+
+template <class E>
+struct LPArgs {
+  using W = typename FT<E>::W;
+  using U = typename KeyT<E>::U;
+  LDev<E> P;
+  const E* __restrict__ y;
+  int K, algo, max_iter;
+  double rel_tol;
+  W* x_out;
+  int* supp_out;
+  int* iters_out;
+  double* res_out;
+  E* h0;            // [batch][N]
+  E* xz;            // [batch][N] zero-filled x (transform path) or NULL
+  uint32_t* bits;   // [batch][N/32] the support (subspace pursuit excludes it)
+  int* S;           // [batch][K] support, ascending, 0 past ns
+  W* xs;            // [batch][K] coefficients
+  E* xsw;           // [batch][K] coefficients in the working precision, 0 past ns
+  U* ckey;          // [batch][ntiles][kmax] tile candidates
+  int* cj;
+  int ntiles, kmax;
+  int* sel;         // [batch][kmax] selection, ascending
+  W* B;             // [batch][mm(mm+1)/2]
+  LState* st;       // done flags
+  LPExtra* ex;
+  double* ypart;
+  int nyp;
+};
+
+__host__ __device__ inline int lp_mmax(int K, int algo) { return algo == 0 ? 2 * K : 3 * K; }
+
+// Each tile's top-k of |src(j)|^2 over j (excluding the support when excl).
+template <class E>
+__global__ void __launch_bounds__(kLT) lp_tile_kernel(LPArgs<E> a, const E* __restrict__ src, int k, int excl) {
+  using U = typename KeyT<E>::U;
+  using V = typename NormT<E>::V;
+  extern __shared__ __align__(16) unsigned char sm[];
+  U* keys = (U*)sm;
+  int* out = (int*)(sm + al16((size_t)kSelTile * sizeof(U)));
+  int* hist = out + al16((size_t)k * sizeof(int)) / sizeof(int);
+  int* scr = hist + 260;
+  const int64_t b = blockIdx.y;
+  if (a.st[b].done) return;
+  const int N = a.P.N, j0 = blockIdx.x * kSelTile;
+  const E* hb = src + b * (int64_t)N;
+  const uint32_t* bb = a.bits + b * (int64_t)(N >> 5);
+  for (int i = threadIdx.x; i < kSelTile; i += kLT) {
+    const int j = j0 + i;
+    keys[i] = (excl && in_bits(bb, j)) ? (U)0 : sel_key((V)norm2(hb[j]));
+  }
+  const Grp g = whole_block();
+  g.sync();
+  group_topk(g, keys, kSelTile, k, out, hist, scr);
+  U* ck = a.ckey + (b * a.ntiles + blockIdx.x) * (int64_t)a.kmax;
+  int* cjj = a.cj + (b * a.ntiles + blockIdx.x) * (int64_t)a.kmax;
+  for (int i = threadIdx.x; i < k; i += kLT) {
+    ck[i] = keys[out[i]];
+    cjj[i] = j0 + out[i];
+  }
+}
+
+// The overall top-k of the tiles' candidates (tile-major, j ascending within
+// a tile, so candidate order is j order) -> sel, ascending.
+template <class E>
+__global__ void __launch_bounds__(kLT) lp_merge_kernel(LPArgs<E> a, int k) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  int* out = (int*)sm;
+  int* hist = out + al16((size_t)k * sizeof(int)) / sizeof(int);
+  int* scr = hist + 260;
+  const int64_t b = blockIdx.x;
+  if (a.st[b].done) return;
+  const Grp g = whole_block();
+  // k == kmax: the tiles' candidates are contiguous
+  const int n = a.ntiles * k;
+  const typename KeyT<E>::U* keys = a.ckey + b * (int64_t)a.ntiles * a.kmax;
+  const int* cjb = a.cj + b * (int64_t)a.ntiles * a.kmax;
+  group_topk(g, keys, n, k, out, hist, scr);
+  for (int i = threadIdx.x; i < k; i += kLT) a.sel[b * (int64_t)a.kmax + i] = cjb[out[i]];
+}
+
+template <class E>
+struct LPLayout {
+  size_t z, x, g, part, lam, sk, T, sel2, hist, scr, red, total;
+  int npart;
+};
+
+template <class E>
+__host__ __device__ inline LPLayout<E> lp_layout(int K, int algo) {
+  using W = typename FT<E>::W;
+  LPLayout<E> L;
+  const int mm = lp_mmax(K, algo);
+  L.npart = 2 * kLT > mm ? 2 * kLT : mm;
+  size_t o = 0;
+  L.z = o;    o = al16(o + (size_t)mm * sizeof(W));
+  L.x = o;    o = al16(o + (size_t)mm * sizeof(W));
+  L.g = o;    o = al16(o + (size_t)mm * sizeof(W));
+  L.part = o; o = al16(o + (size_t)L.npart * sizeof(W) + (size_t)3 * mm * sizeof(double));
+  L.lam = o;  o = al16(o + (size_t)mm * sizeof(int));
+  L.sk = o;   o = al16(o + (size_t)mm * sizeof(unsigned long long));
+  L.T = o;    o = al16(o + (size_t)mm * sizeof(int));
+  L.sel2 = o; o = al16(o + (size_t)mm * sizeof(int));
+  L.hist = o; o = al16(o + 260 * sizeof(int));
+  L.scr = o;  o = al16(o + 34 * sizeof(int));
+  L.red = o;  o = al16(o + (32 * 2 + 2) * sizeof(double));
+  L.total = o;
+  return L;
+}
+
+template <class E>
+__device__ void lp_outputs(const LPArgs<E>& a, int64_t b, const LPExtra& X) {
+  using W = typename FT<E>::W;
+  const int K = a.K, ns = X.ns;
+  for (int k = threadIdx.x; k < K; k += kLT) {
+    if (a.x_out) a.x_out[b * K + k] = k < ns ? a.xs[b * K + k] : W{};
+    a.supp_out[b * K + k] = k < ns ? a.S[b * K + k] : -1;
+  }
+  if (threadIdx.x == 0) {
+    if (a.iters_out) a.iters_out[b] = X.it;
+    if (a.res_out) a.res_out[b] = X.ynorm2 > 0.0 ? sqrt(fmax(X.rn2, 0.0) / X.ynorm2) : 0.0;
+    a.st[b].done = 1;
+  }
+}
+
+// phase 0: ||y||^2, SP's first support (sel) and its least squares; phase 1:
+// one iteration's candidate set (sel with the support), least squares,
+// pruning and the stop rules.
+template <class E>
+__global__ void __launch_bounds__(kLT) lp_step_kernel(LPArgs<E> a, int phase) {
+  using W = typename FT<E>::W;
+  constexpr bool DFT = FT<E>::C;
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ LPExtra X;
+  __shared__ LsShared<W> sh;
+  const int64_t b = blockIdx.x;
+  if (a.st[b].done) return;
+  const int N = a.P.N, K = a.K, mm = lp_mmax(K, a.algo);
+  const LPLayout<E> L = lp_layout<E>(K, a.algo);
+  const Grp g = whole_block();
+  LsView<E> lv;
+  lv.B = a.B + b * (((int64_t)mm * (mm + 1)) >> 1);
+  lv.z = (W*)(sm + L.z);
+  lv.x = (W*)(sm + L.x);
+  lv.g = (W*)(sm + L.g);
+  lv.part = (W*)(sm + L.part);
+  lv.terms = (double*)(lv.part + L.npart);
+  lv.xw = nullptr;
+  lv.lam = (int*)(sm + L.lam);
+  lv.bits = nullptr;
+  lv.kidx = nullptr;
+  unsigned long long* sk = (unsigned long long*)(sm + L.sk);
+  int* T = (int*)(sm + L.T);
+  int* sel2 = (int*)(sm + L.sel2);
+  int* hist = (int*)(sm + L.hist);
+  int* scr = (int*)(sm + L.scr);
+  double* red = (double*)(sm + L.red);
+  PlanDev<E> pd;
+  pd.N = N;
+  pd.logN = a.P.logN;
+  pd.M = a.P.M;
+  pd.slot = a.P.slot;
+  pd.tw = nullptr;
+  pd.c = a.P.c;
+  pd.c64 = a.P.c64;
+  pd.cfmt = a.P.cfmt;
+  pd.ci = a.P.ci;
+  const E* h0 = a.h0 + b * (int64_t)N;
+  int* S = a.S + b * K;
+  W* xs = a.xs + b * K;
+  E* xsw = a.xsw + b * K;
+  uint32_t* bb = a.bits + b * (int64_t)(N >> 5);
+  E* xz = a.xz ? a.xz + b * (int64_t)N : nullptr;
+  const int* sel = a.sel + b * (int64_t)a.kmax;
+  if (threadIdx.x == 0) X = a.ex[b];
+  g.sync();
+  const double tol2 = a.rel_tol * a.rel_tol;
+
+  // least squares on cols[0..m): append them to an empty factor
+  auto ls_set = [&](const int* cols, int m) {
+    if (threadIdx.x == 0) X.ls_rn2 = X.ynorm2;
+    g.sync();
+    int p = 0;
+    for (int c = 0; c < m; ++c) {
+      ls_append(g, pd, lv, h0, p, cols[c], X.ls_rn2, sh);
+      if (sh.st == 0) ++p;
+    }
+    if (threadIdx.x == 0) X.m = p;
+    g.sync();
+  };
+  // the accepted support and coefficients (ns entries, ascending columns)
+  auto set_support = [&](const int* cols, const W* coef, int ns) {
+    for (int k = threadIdx.x; k < X.ns; k += kLT) {  // the old support leaves bits and zf(x)
+      const int j = S[k];
+      if (xz) xz[j] = zero<E>();
+      atomicAnd(bb + (j >> 5), ~(1u << (j & 31)));
+    }
+    g.sync();
+    for (int k = threadIdx.x; k < K; k += kLT) {
+      const int j = k < ns ? cols[k] : 0;
+      const W v = k < ns ? coef[k] : W{};
+      S[k] = j;
+      xs[k] = v;
+      xsw[k] = from_w<E>(v);
+      if (k < ns) {
+        if (xz) xz[j] = from_w<E>(v);
+        atomicOr(bb + (j >> 5), 1u << (j & 31));
+      }
+    }
+    g.sync();
+    if (threadIdx.x == 0) X.ns = ns;
+    g.sync();
+  };
+
+  bool stop = false;
+  if (phase == 0) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < a.nyp; i += kLT) t += a.ypart[b * a.nyp + i];
+    double tt[1] = {t};
+    group_sum(g, tt, red);
+    if (threadIdx.x == 0) {
+      X.ynorm2 = tt[0];
+      X.rn2 = tt[0];
+      X.ns = 0;
+      X.it = 0;
+    }
+    g.sync();
+    if (!(X.ynorm2 > 0.0) || K == 0) {
+      stop = true;
+    } else if (a.algo == 0) {  // SP: T_0 = top_K(h_0), x = LS on T_0
+      for (int i = threadIdx.x; i < K; i += kLT) T[i] = sel[i];
+      g.sync();
+      ls_set(T, K);
+      for (int k = threadIdx.x; k < X.m; k += kLT) sel2[k] = lv.lam[k];
+      g.sync();
+      set_support(sel2, lv.x, X.m);
+      if (threadIdx.x == 0) X.rn2 = X.ls_rn2;
+      g.sync();
+    }
+  } else {
+    const int ns = X.ns, kk = a.algo == 0 ? K : 2 * K;
+    // T = support + selection (both ascending), without duplicates
+    if (threadIdx.x == 0) {
+      int i = 0, j = 0, o = 0;
+      while (i < ns || j < kk) {
+        int v;
+        if (j >= kk || (i < ns && S[i] < sel[j])) v = S[i++];
+        else if (i < ns && S[i] == sel[j]) { v = S[i++]; ++j; }
+        else v = sel[j++];
+        T[o++] = v;
+      }
+      X.m = o;
+    }
+    g.sync();
+    ls_set(T, X.m);                         // b = LS on T (lv.lam, lv.x)
+    const int m = X.m;
+    for (int i = threadIdx.x; i < m; i += kLT) sk[i] = sel_key(norm2(lv.x[i]));
+    g.sync();
+    const int kp = K < m ? K : m;
+    group_topk(g, sk, m, kp, sel2, hist, scr);  // prune: the K largest |b|, ascending positions
+    for (int i = threadIdx.x; i < kp; i += kLT) T[i] = lv.lam[sel2[i]];
+    if (a.algo == 1)
+      for (int i = threadIdx.x; i < kp; i += kLT) lv.g[i] = lv.x[sel2[i]];
+    g.sync();
+    if (a.algo == 0) {
+      ls_set(T, kp);                        // x_new = LS on T_new
+      if (threadIdx.x == 0) X.rn2_new = X.ls_rn2;
+      g.sync();
+    } else {
+      // ||y - Phi x||^2 = ||y||^2 - 2 Re x^H h_0(S) + x^H G_S x  (FP64)
+      double acc[2] = {0.0, 0.0};
+      for (int i = threadIdx.x; i < kp; i += kLT) {
+        const W xi = lv.g[i];
+        acc[0] += re(cmul(xi, to_w(h0[T[i]])));
+        W gx = W{};
+        for (int j = 0; j < kp; ++j) {
+          const int d = DFT ? ((T[i] - T[j]) & (N - 1)) : (T[i] ^ T[j]);
+          gx = fmav(gx, c64_at(pd, d), lv.g[j]);
+        }
+        acc[1] += re(cmul(xi, gx));
+      }
+      group_sum(g, acc, red);
+      if (threadIdx.x == 0) {
+        X.rn2_new = X.ynorm2 - 2.0 * acc[0] + acc[1];
+        X.m = kp;
+      }
+      g.sync();
+    }
+    if (threadIdx.x == 0) X.it = X.it + 1;
+    g.sync();
+    if (!(X.rn2_new < X.rn2)) {
+      stop = true;  // keep the previous iterate
+    } else {
+      if (a.algo == 0) {
+        for (int k = threadIdx.x; k < X.m; k += kLT) sel2[k] = lv.lam[k];
+        g.sync();
+        set_support(sel2, lv.x, X.m);
+      } else {
+        set_support(T, lv.g, kp);
+      }
+      if (threadIdx.x == 0) X.rn2 = X.rn2_new;
+      g.sync();
+    }
+  }
+  if (!stop && (X.it >= a.max_iter || X.rn2 < tol2 * X.ynorm2)) stop = true;
+  if (stop) lp_outputs(a, b, X);
+  if (threadIdx.x == 0) a.ex[b] = X;
+}
+
+template <class E>
+struct LPWs {
+  size_t st, ex, h0, H, T, Z, xz, bits, S, xs, xsw, ck, cj, sel, B, yp, total;
+  int ntiles, kmax, nyp;
+};
+
+template <class E>
+LPWs<E> lp_ws(const PlanView& Pv, int K, int algo, int fast, int64_t batch) {
+  using W = typename FT<E>::W;
+  using U = typename KeyT<E>::U;
+  LPWs<E> L;
+  const size_t N = (size_t)Pv.N, Nv = (size_t)batch * N * (Pv.dft ? 2 : 1) * (Pv.fp32 ? 4 : 8);
+  const int mm = lp_mmax(K, algo);
+  L.ntiles = (int)(N / kSelTile);
+  L.kmax = algo == 0 ? K : 2 * K;
+  {
+    const int64_t g = ((int64_t)Pv.M + 2047) / 2048;
+    L.nyp = (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
+  }
+  size_t o = 0;
+  L.st = o;   o = al16(o + (size_t)batch * sizeof(LState));
+  L.ex = o;   o = al16(o + (size_t)batch * sizeof(LPExtra));
+  L.h0 = o;   o = al16(o + Nv);
+  L.H = o;    o = al16(o + Nv);
+  L.T = o;    o = al16(o + Nv);
+  L.Z = o;    o = al16(o + (fast ? 0 : Nv));
+  L.xz = o;   o = al16(o + (fast ? 0 : Nv));
+  L.bits = o; o = al16(o + (size_t)batch * (N >> 5) * sizeof(uint32_t));
+  L.S = o;    o = al16(o + (size_t)batch * K * sizeof(int));
+  L.xs = o;   o = al16(o + (size_t)batch * K * sizeof(W));
+  L.xsw = o;  o = al16(o + (size_t)batch * K * sizeof(E));
+  L.ck = o;   o = al16(o + (size_t)batch * L.ntiles * L.kmax * sizeof(U));
+  L.cj = o;   o = al16(o + (size_t)batch * L.ntiles * L.kmax * sizeof(int));
+  L.sel = o;  o = al16(o + (size_t)batch * L.kmax * sizeof(int));
+  L.B = o;    o = al16(o + (size_t)batch * (((size_t)mm * (mm + 1)) / 2) * sizeof(W));
+  L.yp = o;   o = al16(o + (size_t)batch * L.nyp * sizeof(double));
+  L.total = o;
+  return L;
+}
+
+template <class E>
+cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStream_t s) {
+  using W = typename FT<E>::W;
+  using U = typename KeyT<E>::U;
+  constexpr bool DFT = FT<E>::C;
+  const LDev<E> P = ldev<E>(Pv);
+  const int64_t batch = q.batch;
+  const LPWs<E> L = lp_ws<E>(Pv, q.K, q.algo, q.fast, batch);
+  unsigned char* w = (unsigned char*)ws;
+  LPArgs<E> a;
+  a.P = P;
+  a.y = (const E*)q.y;
+  a.K = q.K;
+  a.algo = q.algo;
+  a.max_iter = q.max_iter;
+  a.rel_tol = q.rel_tol;
+  a.x_out = (W*)q.x_out;
+  a.supp_out = q.supp_out;
+  a.iters_out = q.iters_out;
+  a.res_out = q.res_out;
+  a.st = (LState*)(w + L.st);
+  a.ex = (LPExtra*)(w + L.ex);
+  a.h0 = (E*)(w + L.h0);
+  E* H = (E*)(w + L.H);
+  E* T = (E*)(w + L.T);
+  E* Z = q.fast ? nullptr : (E*)(w + L.Z);
+  a.xz = q.fast ? nullptr : (E*)(w + L.xz);
+  a.bits = (uint32_t*)(w + L.bits);
+  a.S = (int*)(w + L.S);
+  a.xs = (W*)(w + L.xs);
+  a.xsw = (E*)(w + L.xsw);
+  a.ckey = (U*)(w + L.ck);
+  a.cj = (int*)(w + L.cj);
+  a.ntiles = L.ntiles;
+  a.kmax = L.kmax;
+  a.sel = (int*)(w + L.sel);
+  a.B = (W*)(w + L.B);
+  a.ypart = (double*)(w + L.yp);
+  a.nyp = L.nyp;
+  const size_t Nv = (size_t)batch * P.N * sizeof(E);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(a.st, 0, (size_t)batch * sizeof(LState), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.ex, 0, (size_t)batch * sizeof(LPExtra), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.bits, 0, (size_t)batch * (P.N >> 5) * sizeof(uint32_t), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.S, 0, (size_t)batch * q.K * sizeof(int), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.xsw, 0, (size_t)batch * q.K * sizeof(E), s)) != cudaSuccess) return e;
+  if (Z && (e = cudaMemsetAsync(Z, 0, Nv, s)) != cudaSuccess) return e;
+  if (a.xz && (e = cudaMemsetAsync(a.xz, 0, Nv, s)) != cudaSuccess) return e;
+  const size_t tile_smem = al16((size_t)kSelTile * sizeof(U)) + al16((size_t)a.kmax * sizeof(int)) + 300 * sizeof(int);
+  const size_t merge_smem = al16((size_t)a.kmax * sizeof(int)) + 300 * sizeof(int);
+  const size_t step_smem = lp_layout<E>(q.K, q.algo).total;
+  if ((e = allow_smem(lp_tile_kernel<E>, tile_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(lp_step_kernel<E>, step_smem)) != cudaSuccess) return e;
+  const double isq = inv_sqrt_n(P.logN);
+  const dim3 tgrid((unsigned)L.ntiles, (unsigned)batch);
+  // h_0 = Phi^H y by one transform, and ||y||^2
+  lynorm_kernel<E><<<dim3((unsigned)L.nyp, (unsigned)batch), kLT, 0, s>>>(a.y, P.M, a.ypart, L.nyp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = run_col<E, DFT, LD_ZF>(P, a.y, P.M, T, a.st, batch, s)) != cudaSuccess) return e;
+  if ((e = run_row<E, DFT, SK_H>(P, T, DFT, isq, a.h0, nullptr, nullptr, nullptr, nullptr, 0, a.st, batch, s)) !=
+      cudaSuccess)
+    return e;
+  if (q.algo == 0) {  // SP's first support: top_K(h_0)
+    lp_tile_kernel<E><<<tgrid, kLT, tile_smem, s>>>(a, a.h0, q.K, 0);
+    lp_merge_kernel<E><<<(unsigned)batch, kLT, merge_smem, s>>>(a, q.K);
+  }
+  lp_step_kernel<E><<<(unsigned)batch, kLT, step_smem, s>>>(a, 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int kk = q.algo == 0 ? q.K : 2 * q.K;
+  for (int it = 0; it < q.max_iter; ++it) {
+    if (q.fast) {  // h = h_0 - sum over the support (zero-padded to K atoms)
+      if ((e = run_fast<E, DFT>(P, a.h0, a.S, a.xsw, q.K, q.K, nullptr, H, nullptr, nullptr, 0, a.st, batch, s)) !=
+          cudaSuccess)
+        return e;
+    } else {  // r = y - Phi x by a forward transform of zf(x), then h = A^H zf(r)
+      if ((e = run_col<E, DFT, LD_DENSE>(P, a.xz, P.N, T, a.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, a.y, nullptr, nullptr, nullptr, 0, a.st, batch, s)) !=
+          cudaSuccess)
+        return e;
+      if ((e = run_col<E, DFT, LD_DENSE>(P, Z, P.N, T, a.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_row<E, DFT, SK_H>(P, T, DFT, isq, H, nullptr, nullptr, nullptr, nullptr, 0, a.st, batch, s)) !=
+          cudaSuccess)
+        return e;
+    }
+    lp_tile_kernel<E><<<tgrid, kLT, tile_smem, s>>>(a, H, kk, q.algo == 0);
+    lp_merge_kernel<E><<<(unsigned)batch, kLT, merge_smem, s>>>(a, kk);
+    lp_step_kernel<E><<<(unsigned)batch, kLT, step_smem, s>>>(a, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ entry points
@@ -1159,4 +1617,18 @@ cudaError_t large_omp(const PlanView& P, const OmpLaunch& a, void* ws, cudaStrea
   return P.fp32 ? omp_t<float>(P, a, ws, st) : omp_t<double>(P, a, ws, st);
 }
 
+}  // namespace csf
+
+namespace csf {
+size_t large_pursuit_ws(const PlanView& P, int K, int algo, int fast, int64_t batch) {
+  if (P.dft) return P.fp32 ? lp_ws<float2>(P, K, algo, fast, batch).total : lp_ws<double2>(P, K, algo, fast, batch).total;
+  return P.fp32 ? lp_ws<float>(P, K, algo, fast, batch).total : lp_ws<double>(P, K, algo, fast, batch).total;
+}
+
+cudaError_t large_pursuit(const PlanView& P, const PursuitLaunch& a, void* ws, cudaStream_t st) {
+  if (a.batch <= 0) return cudaSuccess;
+  if (a.batch > kMaxBatchY) return cudaErrorInvalidValue;
+  if (P.dft) return P.fp32 ? lp_t<float2>(P, a, ws, st) : lp_t<double2>(P, a, ws, st);
+  return P.fp32 ? lp_t<float>(P, a, ws, st) : lp_t<double>(P, a, ws, st);
+}
 }  // namespace csf

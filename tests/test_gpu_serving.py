@@ -131,8 +131,8 @@ def test_refusals():
         srv.submit("dft", "fp32", 1 << 16, inst["omega"], inst["Y"][0], 16)
     with pytest.raises(binding.CsError):  # K > M
         srv.submit("wht", "fp64", 64, np.arange(8), np.ones(8), 9)
-    with pytest.raises(binding.CsError):  # CoSaMP beyond one-CTA sizes
-        srv.submit("dft", "fp32", 1 << 16, inst["omega"], inst["Y"][0], 8, algo="cosamp")
+    with pytest.raises(binding.CsError):  # CoSaMP beyond K = 128
+        srv.submit("dft", "fp32", 1 << 16, inst["omega"], inst["Y"][0], 200, algo="cosamp")
     srv.close()
 
 
