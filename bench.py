@@ -327,7 +327,8 @@ def _serving_gen(req):
 def serving(n_req: int, rate: float = 2000.0, workers: int = 8, budget_gb: float = 64.0):
     """The serving workload: Poisson arrivals at 2000 requests/s, N = 2^14 ..
     2^20, M = N/8, K = 32 .. 1024, partial WHT or DFT by a coin, FP32, OMP
-    (hybrid switch), each request with its own Omega, replayed in real time
+    (hybrid switch) or CoSaMP by a coin (CoSaMP's K capped at 128, its limit
+    in the library), each request with its own Omega, replayed in real time
     into the request runtime (cs_server_*) with `workers` streams and a
     device-memory budget; latency = completion - arrival.  The same requests
     are then replayed at half the throughput measured at the offered rate
@@ -352,7 +353,7 @@ def serving(n_req: int, rate: float = 2000.0, workers: int = 8, budget_gb: float
             dt = r["arrival_s"] * scale - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            srv.submit(r["kind"], "fp32", r["N"], om, yv, r["K"])
+            srv.submit(r["kind"], "fp32", r["N"], om, yv, r["K"], algo=r["algo"])
         res = srv.wait_all()
         srv.close()
         lat = sorted((r["t_done_us"] - r["t_submit_us"]) * 1e-3 for r in res)
@@ -365,7 +366,8 @@ def serving(n_req: int, rate: float = 2000.0, workers: int = 8, budget_gb: float
 
     sat = replay(1.0)
     sus = replay(rate / max(1e-9, 0.5 * sat["solves_per_s"]))
-    return {"workload": f"{n_req} requests, Poisson, N=2^14..2^20, M=N/8, K=32..1024, WHT/DFT fp32, OMP",
+    return {"workload": f"{n_req} requests, Poisson, N=2^14..2^20, M=N/8, K=32..1024, WHT/DFT fp32, "
+                        "OMP or CoSaMP (CoSaMP K capped at 128)",
             "workers": workers, "budget_gb": budget_gb, "at_offered_rate": sat, "at_half_saturation": sus}
 
 

@@ -123,10 +123,11 @@ CONFIG_DFT_C64_BATCH = dict(kind=DFT, N=4096, M=1024, K=64, B=1024, snr_db=40.0,
 
 # Request stream of the serving workload: Poisson arrivals at `rate` per
 # second; N = 2^e with e uniform over [log_n_lo, log_n_hi]; M = N / 8; K
-# uniform over [k_lo, k_hi]; kind by a fair coin; noiseless Gaussian
-# nonzeros; each request has its own Omega and seed.
+# uniform over [k_lo, k_hi]; kind by a fair coin; OMP or CoSaMP by a fair
+# coin, CoSaMP's K capped at cosamp_k_max; noiseless Gaussian nonzeros; each
+# request has its own Omega and seed.
 def serving_requests(n: int, rate: float = 2000.0, seed: int = 0, log_n_lo: int = 14, log_n_hi: int = 20,
-                     k_lo: int = 32, k_hi: int = 1024) -> list[dict]:
+                     k_lo: int = 32, k_hi: int = 1024, cosamp_k_max: int = 128) -> list[dict]:
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=n))
     out = []
@@ -135,7 +136,11 @@ def serving_requests(n: int, rate: float = 2000.0, seed: int = 0, log_n_lo: int 
         M = N // 8
         K = int(min(rng.integers(k_lo, k_hi + 1), M))
         kind = DFT if rng.integers(0, 2) else WHT
-        out.append({"arrival_s": float(t[i]), "kind": kind, "N": N, "M": M, "K": K, "seed": seed * 100003 + i + 1})
+        algo = "cosamp" if rng.integers(0, 2) else "omp"
+        if algo == "cosamp":
+            K = min(K, cosamp_k_max, M // 3)
+        out.append({"arrival_s": float(t[i]), "kind": kind, "N": N, "M": M, "K": K, "algo": algo,
+                    "seed": seed * 100003 + i + 1})
     return out
 
 
