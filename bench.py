@@ -146,10 +146,11 @@ def correlation_flops(N: int, iters: np.ndarray, t_switch: int, path: str) -> fl
 
 
 def flush_l2(buf):
+    import torch
     """Evicts L2: write a buffer twice the L2 size, then read it, leaving L2
     full of clean lines that belong to no input of the timed step."""
     buf.zero_()
-    buf.sum()
+    buf.view(torch.float32).sum()  # read back as float32: no widening copy
 
 
 def _events_ms(fn, steps, warmup, stream, flush=None):
