@@ -643,8 +643,14 @@ __device__ bool ls_u_phase(const LOmpArgs<E>& a, int nparts, int G, int gi, int6
   double an = 0.0, ar = 0.0, ai = 0.0;
   for (int i = r0 + w; i < r1; i += kLT / 32) {
     const W* Bi = B + pidx(i);
-    W acc = W{};
-    for (int k = lane; k <= i; k += 32) acc = fmav(acc, Bi[k], gk[k]);
+    W acc = W{}, acc2 = W{};  // two independent chains: FP64 latency, not issue, bounds one row
+    int k = lane;
+    for (; k + 32 <= i; k += 64) {
+      acc = fmav(acc, Bi[k], gk[k]);
+      acc2 = fmav(acc2, Bi[k + 32], gk[k + 32]);
+    }
+    if (k <= i) acc = fmav(acc, Bi[k], gk[k]);
+    acc = add(acc, acc2);
     const double sr = warp_sum(re(acc));
     const double si = DFT ? warp_sum(im(acc)) : 0.0;
     if (lane == 0) {
@@ -713,26 +719,52 @@ __device__ void ls_w_phase(const LOmpArgs<E>& a, int G, int gi, int64_t b) {
   __shared__ W wpart[RG][32];
   const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
   const int k0 = col_cut(p, gi, G), k1 = col_cut(p, gi + 1, G);
-  for (int kw = k0; kw < k1; kw += 32) {
-    const int k = kw + lane;
-    W acc = W{};
-    if (k < k1)
-      for (int i = kw + rg; i < p; i += RG)
-        if (i >= k) acc = fmacv(acc, u[i], B[pidx(i) + k]);
-    wpart[rg][lane] = acc;
-    __syncthreads();
-    if (rg == 0 && k < k1) {
-      W sum = wpart[0][lane];
-      for (int r = 1; r < RG; ++r) sum = add(sum, wpart[r][lane]);
-      const W wk = scale(sum, -invd);
-      B[pidx(p) + k] = wk;
-      const W xk = fmacv(x[k], wk, zeta);
-      x[k] = xk;
-      const E e = from_w<E>(xk);
-      xw[k] = e;
-      if (xz) xz[lam[k]] = e;
+  // the new row's entry and the coefficient update for column k
+  auto finish = [&](int k, const W& sum) {
+    const W wk = scale(sum, -invd);
+    B[pidx(p) + k] = wk;
+    const W xk = fmacv(x[k], wk, zeta);
+    x[k] = xk;
+    const E e = from_w<E>(xk);
+    xw[k] = e;
+    if (xz) xz[lam[k]] = e;
+  };
+  if (k1 - k0 >= 32 * RG) {
+    // wide block: strips of 32 columns over the lanes (one contiguous segment
+    // of each row), every 8th row per warp, the 8 partial sums of a column
+    // added in shared memory in a fixed order
+    for (int kw = k0; kw < k1; kw += 32) {
+      const int k = kw + lane;
+      W acc = W{};
+      if (k < k1)
+        for (int i = kw + rg; i < p; i += RG)
+          if (i >= k) acc = fmacv(acc, u[i], B[pidx(i) + k]);
+      wpart[rg][lane] = acc;
+      __syncthreads();
+      if (rg == 0 && k < k1) {
+        W sum = wpart[0][lane];
+        for (int r = 1; r < RG; ++r) sum = add(sum, wpart[r][lane]);
+        finish(k, sum);
+      }
+      __syncthreads();
     }
-    __syncthreads();
+  } else {
+    // narrow block (a few long columns): one column per warp, the lanes over
+    // its rows, so that no FP64 lane idles (a masked FP64 lane costs as much
+    // as an active one)
+    for (int k = k0 + rg; k < k1; k += RG) {
+      W acc = W{}, acc2 = W{};
+      int i = k + lane;
+      for (; i + 32 < p; i += 64) {
+        acc = fmacv(acc, u[i], B[pidx(i) + k]);
+        acc2 = fmacv(acc2, u[i + 32], B[pidx(i + 32) + k]);
+      }
+      if (i < p) acc = fmacv(acc, u[i], B[pidx(i) + k]);
+      acc = add(acc, acc2);
+      const double sr = warp_sum(re(acc));
+      const double si = FT<E>::C ? warp_sum(im(acc)) : 0.0;
+      if (lane == 0) finish(k, make_w<W>(sr, si));
+    }
   }
   if (gi == 0 && threadIdx.x == 0) {
     B[pidx(p) + p] = make_w<W>(invd, 0.0);
