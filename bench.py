@@ -1,6 +1,6 @@
 """Benchmark: batched OMP on partial-DFT measurements, fast vs FFT correlation.
 
-Workload (the configuration the headline metric is quoted on): partial DFT,
+Workload of the headline metric: partial DFT,
 complex64 correlation side, 1024 instances sharing one Omega, N = 4096,
 M = 1024 random rows, K = 64, complex Gaussian nonzeros, 40 dB AWGN, halt at K
 or ||r|| < 1e-6 ||y||.  One step = one cs_omp call on the whole batch: the
@@ -253,12 +253,12 @@ def _uneven_gen(spec):
 
 
 def uneven(n_inst: int, workers: int = 8, budget_gb: float = 64.0):
-    """The uneven batch (BASELINE's third configuration, a sample of it):
+    """The uneven batch of mixed plans (a sample of 1024 of its 4096 instances):
     N = 2^12 .. 2^16, M = N/4 or N/8, K = 8 .. 256, WHT FP32 or DFT complex64,
     per-instance Omega, noiseless, all submitted at once to the request
     runtime, which runs them concurrently on `workers` streams (one plan and
-    one solve per instance: not the single persistent launch the
-    configuration describes)."""
+    one solve per instance, run concurrently, rather than one persistent
+    launch over all instances)."""
     from paper_1205_4139_gb300 import binding
     specs = synth.uneven_batch(n_inst, seed=0)
     ctx = mp.get_context("spawn")
@@ -282,7 +282,7 @@ def uneven(n_inst: int, workers: int = 8, budget_gb: float = 64.0):
 
 
 def config5(N=1 << 22, M=1 << 19, K=4096):
-    """BASELINE's fifth configuration, once: one partial-DFT complex64
+    """The one large instance, once: one partial-DFT complex64
     instance, N = 2^22, M = 2^19, K = 4096, 30 dB, OMP (hybrid at the tuned
     switch point of a K = 256 run) with the FP64 least squares on the GPU.
     The FP64 oracle cannot run it (Phi_Lambda alone is 2^19 x 4096), so the
