@@ -159,8 +159,11 @@ cs_status cs_correlate_fast(cs_plan_t plan, const void* h0_dev, const int32_t* s
                             int32_t* argmax_dev, void* stream);
 
 /* OMP (Algorithm 1.1) on `batch` measurements y (F[M] each) sharing the
- * plan's Omega, one fused persistent kernel for the whole batch.  Outputs per
- * instance b:
+ * plan's Omega.  For N <= 8192 the whole batch is one fused persistent kernel:
+ * one CTA per instance, or for batch <= 19 and K <= 256 eight CTAs of a
+ * cluster per instance (same results bit for bit).  Larger plans run each
+ * iteration as a few whole-GPU launches (four-step transform passes,
+ * kernel-sum pass, least-squares phases).  Outputs per instance b:
  *   x_dev      FP64 coefficients [K] in selection order (double or
  *              interleaved complex double), zero past iters
  *   supp_dev   int32 [K] support in selection order, -1 past iters
@@ -176,7 +179,7 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
                  void* stream);
 
 /* Subspace pursuit and CoSaMP on `batch` measurements sharing the plan's
- * Omega, one CTA per instance.  The paper applies its correlation to these
+ * Omega, one CTA per instance for N <= 8192.  The paper applies its correlation to these
  * algorithms (Sec. I) and reports the cost of a fast CoSaMP (Sec. IV) without
  * defining them; they take their standard forms:
  *   SP:     T = top_K(Phi^H y), x = LS on T; each iteration T' = T + top_K of
