@@ -178,6 +178,37 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
                  void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev,
                  void* stream);
 
+/* OMP (Algorithm 1.1) on `count` independent instances that each have their
+ * own plan (own Omega, N, M, kind and precision) and their own K: an uneven
+ * batch.  The instances of one element type (kind, precision) run in one
+ * persistent kernel, two instances per CTA, taken longest first; the element
+ * types present run one after another on `stream`.  Instance b gets the
+ * outputs cs_omp gives for (plans[b], y_dev[b], K[b]):
+ *   plans      host array [count] of plans on the current device (a plan may
+ *              appear more than once); N <= 2^16; plans with N > 8192 need
+ *              the full storage of c (no CS_PLAN_C_* flag)
+ *   y_dev      host array [count] of device pointers, F[M_b] each
+ *   K          host array [count], 0 <= K[b] <= min(M_b, 1024)
+ *   x_dev      NULL, or host array [count] of device pointers, FP64 [K[b]]
+ *   supp_dev   host array [count] of device pointers, int32 [K[b]] (an
+ *              entry may be NULL where K[b] = 0)
+ *   iters_dev, resnorm_dev  device arrays [count], indexed by b (each NULL
+ *              allowed)
+ * halt as in cs_omp; with t_switch < 0 an instance takes its plan's switch
+ * point (N <= 8192) or 16 (larger N: their kernel sums stream c through L2).
+ * Instances with N <= 8192 give bit for bit the results of cs_omp on their
+ * plan.  Larger ones run the one-CTA radix-16 chains on buffers in global
+ * memory, where cs_omp runs four-step transforms, and agree with it to
+ * rounding.  The workspace is allocated stream-ordered on `stream` and freed
+ * after the launches.  The call may wait for `stream` while it copies the
+ * instance table.  A device-detected error goes to plans[0]'s status word
+ * (cs_plan_status).  Errors: CS_ERR_INVALID for bad arguments,
+ * CS_ERR_UNSUPPORTED beyond the limits (message in cs_last_error). */
+cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const void* const* y_dev,
+                         const int32_t* K, const cs_halt* halt, void* const* x_dev,
+                         int32_t* const* supp_dev, int32_t* iters_dev, double* resnorm_dev,
+                         void* stream);
+
 /* Subspace pursuit and CoSaMP on `batch` measurements sharing the plan's
  * Omega, one CTA per instance for N <= 8192.  The paper applies its correlation to these
  * algorithms (Sec. I) and reports the cost of a fast CoSaMP (Sec. IV) without

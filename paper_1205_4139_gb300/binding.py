@@ -23,7 +23,7 @@ PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 
 # Every function include/csfast.h declares.
 EXPORTS = ["cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_switch", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
-           "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
+           "cs_correlate_fast", "cs_omp", "cs_omp_batched", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
            "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy",
            "cs_admit_next", "cs_status_string", "cs_last_error"]
 
@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH):
     L.cs_correlate_fast.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, vp]
     L.cs_omp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_omp_noalloc.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
+    L.cs_omp_batched.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp), pi32, ctypes.POINTER(Halt),
+                                 ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
     L.cs_sp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_cosamp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_plan_tune.argtypes = [vp, vp, i64, i32, ctypes.c_double, pi32, pi32, ctypes.POINTER(ctypes.c_float), i32,
@@ -91,8 +93,8 @@ def load(path: str = LIB_PATH):
     L.cs_admit_next.argtypes = [pi64, pi32, i32, i64, i64, i32]
     L.cs_admit_next.restype = ctypes.c_int32
     for f in ("cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_switch", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
-              "cs_correlate_fast", "cs_omp", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
-              "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy"):
+              "cs_correlate_fast", "cs_omp", "cs_omp_batched", "cs_sp", "cs_cosamp", "cs_omp_noalloc",
+              "cs_plan_tune", "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy"):
         getattr(L, f).restype = ctypes.c_int
     L.cs_status_string.argtypes = [ctypes.c_int]
     L.cs_status_string.restype = ctypes.c_char_p
@@ -266,6 +268,46 @@ class Plan:
         res = torch.empty(B, dtype=torch.float64, device="cuda")
         self.pursuit_into(algo, y, K, x, supp, iters, res, rel_tol, path, max_iter, stream=stream)
         return x, supp, iters, res
+
+
+class Batch:
+    """Outputs of cs_omp_batched for a list of instances with their own plans,
+    preallocated so that the call itself can be repeated (timed, captured):
+    x[b] FP64 [K_b], supp[b] int32 [K_b], iters int32 [count], resnorm FP64
+    [count]."""
+
+    def __init__(self, plans, ys, Ks):
+        import torch
+        if not (len(plans) == len(ys) == len(Ks)):
+            raise ValueError("plans, ys and Ks differ in length")
+        for p, y in zip(plans, ys):
+            if y.dtype != p.dtype or y.ndim != 1 or y.shape[0] != p.M or not y.is_cuda or not y.is_contiguous():
+                raise ValueError("each y must be a contiguous CUDA vector of its plan's M and working type")
+        n = len(plans)
+        self.plans, self.ys, self.Ks = list(plans), list(ys), [int(k) for k in Ks]
+        self.x = [torch.zeros(k, dtype=ls_dtype(p.kind), device="cuda") for p, k in zip(plans, self.Ks)]
+        self.supp = [torch.full((k,), -1, dtype=torch.int32, device="cuda") for k in self.Ks]
+        self.iters = torch.zeros(n, dtype=torch.int32, device="cuda")
+        self.resnorm = torch.zeros(n, dtype=torch.float64, device="cuda")
+        vpa = ctypes.c_void_p * max(n, 1)
+        self._plans = vpa(*[p._h.value for p in plans])
+        self._y = vpa(*[y.data_ptr() for y in ys])
+        self._x = vpa(*[t.data_ptr() if t.numel() else None for t in self.x])
+        self._s = vpa(*[t.data_ptr() if t.numel() else None for t in self.supp])
+        self._K = (ctypes.c_int32 * max(n, 1))(*self.Ks)
+
+    def run(self, rel_tol: float = 1e-6, path: str = "hybrid", t_switch: int = -1, stream=None):
+        """cs_omp_batched on the instances (asynchronous on the stream)."""
+        hl = Halt(rel_tol, PATHS[path], t_switch, 0)
+        _check(load().cs_omp_batched(self._plans, len(self.plans), self._y, self._K, ctypes.byref(hl), self._x,
+                                     self._s, _ptr(self.iters), _ptr(self.resnorm), _stream(stream)))
+        return self
+
+
+def omp_batched(plans, ys, Ks, rel_tol: float = 1e-6, path: str = "hybrid", t_switch: int = -1, stream=None):
+    """OMP on instances that each have their own plan and K (cs_omp_batched);
+    returns a Batch with x, supp (lists), iters and resnorm."""
+    return Batch(plans, ys, Ks).run(rel_tol, path, t_switch, stream)
 
 
 def admit_next(footprints, bypassed, in_use: int, budget: int, max_bypass: int = 8) -> int:

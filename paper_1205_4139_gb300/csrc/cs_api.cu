@@ -22,6 +22,7 @@ struct cs_plan_s {
   int t_switch_default;
   int t_switch_tuned = -1;  // set by cs_plan_tune
   int* d_slot = nullptr;
+  int* d_slot_chain = nullptr;  // 8192 < N <= 2^16, DFT: slot map in the one-CTA chains' order
   void* d_tw64 = nullptr;
   void* d_tw32 = nullptr;
   void* d_c64 = nullptr;
@@ -108,8 +109,8 @@ static int plan_switch(const cs_plan_s* p) {
 
 static void plan_free(cs_plan_s* p) {
   if (!p) return;
-  void* bufs[] = {p->d_slot, p->d_tw64, p->d_tw32, p->d_c64, p->d_c32, p->d_ci, p->d_lt64, p->d_lt32, p->d_status,
-                  p->ws};
+  void* bufs[] = {p->d_slot, p->d_slot_chain, p->d_tw64, p->d_tw32, p->d_c64,   p->d_c32,
+                  p->d_ci,   p->d_lt64,       p->d_lt32, p->d_status, p->ws};
   for (void* b : bufs) {
     if (!b) continue;
     if (p->ordered) cudaFreeAsync(b, p->home);
@@ -200,6 +201,19 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
   PLAN_TRY(plan_alloc(p, (void**)&p->d_slot, (size_t)N * sizeof(int32_t)), "cudaMalloc slot");
   PLAN_TRY(cudaMemcpyAsync(p->d_slot, slot.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, st),
            "copy slot");
+  // plans up to 2^16 also run whole instances on one SM in cs_omp_batched,
+  // with the one-CTA chains: their DFT positions and the shared twiddles
+  const bool chain = large && logN <= kMaxLogNMulti;
+  std::vector<int32_t> slot_chain;
+  if (chain && kind == CS_DFT) {
+    slot_chain.assign((size_t)N, -1);
+    for (int64_t m = 0; m < M; ++m) slot_chain[(size_t)dif_position(omega_host[m], logN)] = (int32_t)m;
+    PLAN_TRY(plan_alloc(p, (void**)&p->d_slot_chain, (size_t)N * sizeof(int32_t)), "cudaMalloc slot");
+    PLAN_TRY(cudaMemcpyAsync(p->d_slot_chain, slot_chain.data(), (size_t)N * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, st),
+             "copy slot");
+    PLAN_TRY(chain_twiddles(logN, st, &p->v.ctw64, &p->v.ctw32), "chain twiddles");
+  }
   if (kind == CS_DFT && !large) {
     PLAN_TRY(plan_alloc(p, &p->d_tw64, (size_t)N * sizeof(double2)), "cudaMalloc twiddles");
     if (prec == CS_FP32) PLAN_TRY(plan_alloc(p, &p->d_tw32, (size_t)N * sizeof(float2)), "cudaMalloc twiddles");
@@ -226,6 +240,13 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
   p->v.lt64 = p->d_lt64;
   p->v.lt32 = p->d_lt32;
   p->v.ci = p->d_ci;
+  if (!large) {
+    p->v.slot_chain = p->d_slot;
+    p->v.ctw64 = p->d_tw64;
+    p->v.ctw32 = p->d_tw32;
+  } else if (chain) {
+    p->v.slot_chain = kind == CS_DFT ? p->d_slot_chain : p->d_slot;
+  }
   // c in FP64, full length: into the plan's own buffer (CFMT_FULL) or a
   // scratch vector that is then put into the plan's storage format
   {
@@ -315,6 +336,7 @@ size_t solve_footprint(int64_t N, int64_t M, int32_t kind, int32_t prec, int32_t
     b += (((size_t)1 << v.n1) + ((size_t)1 << v.n2) + ((size_t)1 << v.wsh) + ((size_t)N >> v.wsh)) *
          (16 + (v.fp32 ? 8 : 0));
   if (v.large) b += (size_t)N * wb;  // kernel-vector scratch while the plan is built
+  if (v.dft && v.large && logN <= kMaxLogNMulti) b += (size_t)N * 4;  // chain-order slot map
   size_t ws = 0;
   if (algo == 0) ws = v.large ? large_omp_ws(v, K, CS_PATH_HYBRID, 1) : omp_workspace_bytes(v, K, 1);
   else if (v.large) ws = large_pursuit_ws(v, K, algo == 2 ? 0 : 1, 0, 1);
@@ -464,6 +486,70 @@ extern "C" cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, in
   if (plan->v.large) CS_CUDA(large_omp(plan->v, a, plan->ws, st), "omp kernels");
   else if (cluster) CS_CUDA(launch_omp_cluster(plan->v, a, plan->ws, st), "omp cluster kernel");
   else CS_CUDA(launch_omp(plan->v, a, plan->ws, grid, st), "omp kernel");
+  return CS_OK;
+}
+
+extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const void* const* y_dev,
+                                    const int32_t* K, const cs_halt* halt, void* const* x_dev,
+                                    int32_t* const* supp_dev, int32_t* iters_dev, double* resnorm_dev,
+                                    void* stream) {
+  if (count < 0 || count > ((int64_t)1 << 30)) return CS_ERR_INVALID;
+  cs_halt h = {1e-6, CS_PATH_HYBRID, -1, 0};
+  if (halt) h = *halt;
+  if (!(h.rel_tol >= 0.0) || !std::isfinite(h.rel_tol)) return CS_ERR_INVALID;
+  if (h.path != CS_PATH_FAST && h.path != CS_PATH_CONV && h.path != CS_PATH_HYBRID) return CS_ERR_INVALID;
+  if (count == 0) return CS_OK;
+  if (!plans || !y_dev || !K || !supp_dev) return CS_ERR_INVALID;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  // one launch per element type: (kind, precision)
+  std::vector<MultiItem> group[4];
+  for (int64_t b = 0; b < count; ++b) {
+    const cs_plan_s* p = plans[b];
+    if (!p) return CS_ERR_INVALID;
+    if (p->device != dev) {
+      set_last_error("cs_omp_batched: every plan must live on the current device");
+      return CS_ERR_INVALID;
+    }
+    const int k = K[b];
+    if (k < 0 || k > p->v.M) return CS_ERR_INVALID;
+    if (p->v.M > 0 && !y_dev[b]) return CS_ERR_INVALID;
+    if (k > 0 && (!supp_dev[b] || (x_dev && !x_dev[b]))) return CS_ERR_INVALID;
+    if (p->v.logN > kMaxLogNMulti || k > kMaxK) {
+      set_last_error("cs_omp_batched: N above 2^16 or K above 1024");
+      return CS_ERR_UNSUPPORTED;
+    }
+    if (p->v.large && p->v.cfmt != CFMT_FULL) {
+      set_last_error("cs_omp_batched: plans with N > 8192 need the full storage of c");
+      return CS_ERR_UNSUPPORTED;
+    }
+    MultiItem it;
+    it.P = &p->v;
+    it.y = y_dev[b];
+    it.x = x_dev ? x_dev[b] : nullptr;
+    it.supp = supp_dev[b];
+    it.K = k;
+    it.t_switch = h.t_switch >= 0 ? h.t_switch : (p->v.large ? multi_switch_big(p->v.logN) : plan_switch(p));
+    it.idx = (int)b;
+    it.cost = multi_cost(p->v, k, it.t_switch, h.path);
+    group[(p->v.dft ? 2 : 0) + (p->v.fp32 ? 0 : 1)].push_back(it);
+  }
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  for (auto& g : group) {
+    if (g.empty()) continue;
+    if (omp_multi_smem(g.data(), (int64_t)g.size(), h.path) > (size_t)optin) {
+      set_last_error("cs_omp_batched: N and K of one element type need more shared memory than a CTA has");
+      return CS_ERR_UNSUPPORTED;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (auto& g : group) {
+    if (g.empty()) continue;
+    CS_CUDA(launch_omp_multi(g.data(), (int64_t)g.size(), h.rel_tol, h.path, iters_dev, resnorm_dev,
+                             plans[0]->v.status, st),
+            "omp_batched kernel");
+  }
   return CS_OK;
 }
 

@@ -12,6 +12,7 @@ constexpr int kMaxLogNLarge = 24;  // four-step transforms through global memory
 constexpr int kMaxK = 1024;
 constexpr int kMaxKLarge = 4096;       // large plans: the factor lives in global memory
 constexpr int kMaxLargeBatch = 65535;  // large plans: instances per call
+constexpr int kMaxLogNMulti = 16;      // cs_omp_batched: one CTA per instance up to N = 2^16
 
 // Type-erased view of a plan's device tables.
 struct PlanView {
@@ -36,6 +37,13 @@ struct PlanView {
   // integers N c(d) and c64 / c32 are unused
   int cfmt;
   const int* ci;
+  // the one-CTA radix-16 chains (N <= 2^16): slot map in the chains' position
+  // order and, for DFT, the chains' twiddles (FP64 / FP32).  For N <= 8192
+  // these are slot / tw64 / tw32; for 8192 < N <= 2^16 the slot map is the
+  // plan's own and the twiddles are shared by all plans of that N; NULL above.
+  const int* slot_chain;
+  const void* ctw64;
+  const void* ctw32;
 };
 
 enum { CFMT_FULL = 0, CFMT_HALF = 1, CFMT_INT = 2 };
@@ -100,6 +108,26 @@ constexpr int kClusterMaxK = 256;     // every CTA keeps its own FP64 factor
 size_t omp_cluster_smem(const PlanView& P, int K, int path);
 size_t omp_cluster_workspace_bytes(const PlanView& P, int K, int64_t batch);
 cudaError_t launch_omp_cluster(const PlanView& P, const OmpLaunch& a, void* ws, cudaStream_t st);
+
+// OMP on instances with their own plans (cs_omp_multi.cu).  One item per
+// instance; items of one element type go to one launch.
+struct MultiItem {
+  const PlanView* P;
+  const void* y;
+  void* x;
+  int* supp;
+  int K, t_switch, idx;
+  double cost;  // estimated work, for the longest-first order
+};
+// Chain twiddles of the one-CTA radix-16 DFT chains for N = 2^logN, built on
+// first use per device and kept until the process exits.
+cudaError_t chain_twiddles(int logN, cudaStream_t st, const void** tw64, const void** tw32);
+// Switch point of instances whose buffers live in global memory (N > 8192).
+int multi_switch_big(int logN);
+double multi_cost(const PlanView& P, int K, int t_switch, int path);
+size_t omp_multi_smem(const MultiItem* it, int64_t n, int path);
+cudaError_t launch_omp_multi(MultiItem* it, int64_t n, double rel_tol, int path, int* iters_out, double* res_out,
+                             int* status, cudaStream_t st);
 
 // large plans (cs_large.cu)
 cudaError_t large_tables(const PlanView& P, void* lt64, void* lt32, cudaStream_t st);

@@ -52,6 +52,11 @@ def test_host_side_validation_without_gpu():
     assert L.cs_plan_create(1 << 25, None, 0, 1, 1, None, ctypes.byref(h)) == 4  # beyond N limit (2^24)
     assert L.cs_plan_create(16, None, 0, 2, 1, None, ctypes.byref(h)) == 1   # bad kind
     assert L.cs_omp(None, None, 1, 4, None, None, None, None, None, None) == 1
+    assert L.cs_omp_batched(None, -1, None, None, None, None, None, None, None, None) == 1  # negative count
+    assert L.cs_omp_batched(None, 0, None, None, None, None, None, None, None, None) == 0   # empty batch
+    assert L.cs_omp_batched(None, 2, None, None, None, None, None, None, None, None) == 1   # missing arrays
+    bad = binding.Halt(-1.0, 2, -1, 0)
+    assert L.cs_omp_batched(None, 0, None, None, ctypes.byref(bad), None, None, None, None, None) == 1
     om4 = (ctypes.c_int32 * 2)(1, 5)
     assert L.cs_plan_create_ex(16, om4, 2, 0, 0, 1, None, ctypes.byref(h)) == 1   # half storage on a WHT plan
     assert L.cs_plan_create_ex(16, om4, 2, 1, 0, 2, None, ctypes.byref(h)) == 1   # integer storage on a DFT plan
