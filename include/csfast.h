@@ -91,7 +91,10 @@ typedef struct {
  * fused kernel per call); larger plans spread each instance over the GPU
  * with four-step transforms through global memory and queue a short
  * sequence of kernels per iteration (at most 65535 instances per call;
- * cs_omp_noalloc returns CS_ERR_UNSUPPORTED for them). */
+ * cs_omp_noalloc returns CS_ERR_UNSUPPORTED for them).  Plans with
+ * 8192 < N <= 2^16 also keep the tables cs_omp_batched runs them with on one
+ * SM (a DFT plan: its slot map in the one-CTA chains' order; the chains'
+ * twiddles are built once per N and device and shared by all plans). */
 cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind,
                          int32_t prec, void* stream, cs_plan_t* out);
 
@@ -111,8 +114,9 @@ enum { CS_PLAN_C_HALF = 1u, CS_PLAN_C_INT = 2u };
 cs_status cs_plan_create_ex(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
                             uint32_t flags, void* stream, cs_plan_t* out);
 
-/* Device bytes held by the plan's tables (slot map, c in its storage format,
- * twiddles, status word), not counting the workspace. */
+/* Device bytes held by the plan's tables (slot maps, c in its storage format,
+ * twiddles, status word), not counting the workspace or the chain twiddles
+ * shared by all plans of one N. */
 cs_status cs_plan_memory(cs_plan_t plan, int64_t* table_bytes);
 
 /* Release the plan's device memory (synchronises the device first). */
@@ -180,9 +184,10 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
 
 /* OMP (Algorithm 1.1) on `count` independent instances that each have their
  * own plan (own Omega, N, M, kind and precision) and their own K: an uneven
- * batch.  The instances of one element type (kind, precision) run in one
- * persistent kernel, two instances per CTA, taken longest first; the element
- * types present run one after another on `stream`.  Instance b gets the
+ * batch.  The instances of one element type (kind, precision) and residence
+ * (N <= 8192 in shared memory, larger N in global memory) run in one
+ * persistent kernel, two instances per CTA, taken longest first; the launches
+ * run one after another on `stream`.  Instance b gets the
  * outputs cs_omp gives for (plans[b], y_dev[b], K[b]):
  *   plans      host array [count] of plans on the current device (a plan may
  *              appear more than once); N <= 2^16; plans with N > 8192 need
@@ -195,10 +200,11 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
  *   iters_dev, resnorm_dev  device arrays [count], indexed by b (each NULL
  *              allowed)
  * halt as in cs_omp; with t_switch < 0 an instance takes its plan's switch
- * point (N <= 8192) or 16 (larger N: their kernel sums stream c through L2).
+ * point (N <= 8192) or 32 (larger N: their kernel sums stream c through L2).
  * Instances with N <= 8192 give bit for bit the results of cs_omp on their
- * plan.  Larger ones run the one-CTA radix-16 chains on buffers in global
- * memory, where cs_omp runs four-step transforms, and agree with it to
+ * plan.  Larger ones run the one-CTA radix-16 chains on vectors in global
+ * memory, two passes per round trip through a shared-memory tile, where
+ * cs_omp runs four-step transforms over the GPU, and agree with it to
  * rounding.  The workspace is allocated stream-ordered on `stream` and freed
  * after the launches.  The call may wait for `stream` while it copies the
  * instance table.  A device-detected error goes to plans[0]'s status word

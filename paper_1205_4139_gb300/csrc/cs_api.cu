@@ -502,8 +502,9 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
   if (!plans || !y_dev || !K || !supp_dev) return CS_ERR_INVALID;
   int dev = 0;
   cudaGetDevice(&dev);
-  // one launch per element type: (kind, precision)
-  std::vector<MultiItem> group[4];
+  // one launch per element type (kind, precision) and residence (instances
+  // held in shared memory, N <= 8192, or in global memory)
+  std::vector<MultiItem> group[8];
   for (int64_t b = 0; b < count; ++b) {
     const cs_plan_s* p = plans[b];
     if (!p) return CS_ERR_INVALID;
@@ -532,7 +533,7 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
     it.t_switch = h.t_switch >= 0 ? h.t_switch : (p->v.large ? multi_switch_big(p->v.logN) : plan_switch(p));
     it.idx = (int)b;
     it.cost = multi_cost(p->v, k, it.t_switch, h.path);
-    group[(p->v.dft ? 2 : 0) + (p->v.fp32 ? 0 : 1)].push_back(it);
+    group[(p->v.dft ? 4 : 0) + (p->v.fp32 ? 0 : 2) + (p->v.large ? 1 : 0)].push_back(it);
   }
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

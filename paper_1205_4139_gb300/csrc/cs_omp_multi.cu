@@ -15,17 +15,19 @@
 //     that the instances that start last are short ones;
 //   * c is staged in shared memory per plan, again whenever the correlation
 //     group turns to a slot of another plan;
-//   * instances with N > 8192 keep their transform buffer, support bitmap and
-//     position map in global memory (one buffer per CTA, the others per
-//     slot; they stay in L2 for the most part) and read c straight from the
-//     plan: their transforms are the same radix-16 chains run on that buffer,
-//     and their kernel sums stream c through L2.
+//   * instances with N > 8192 keep their transform vector, support bitmap and
+//     position map in global memory (one vector per CTA, the others per slot;
+//     they stay in L2 for the most part) and read c straight from the plan:
+//     their transforms are the same radix-16 chains, two passes per round
+//     trip through a shared-memory tile (cs_gchain.cuh), and their kernel
+//     sums stream c through L2.
 #include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
 #include <vector>
 
+#include "cs_gchain.cuh"
 #include "cs_internal.h"
 #include "cs_ls.cuh"
 
@@ -59,6 +61,7 @@ struct MArgs {
   int path;
   int Nsm;    // largest N of the instances kept in shared memory (0: none)
   int Nbig;   // largest N of the instances kept in global memory (0: none)
+  int gtile;  // 1: those instances transform through a shared-memory stage tile
   int Nmax, Kmax;
   int* iters_out;             // [count], by instance index (nullable)
   double* res_out;            // [count] (nullable)
@@ -73,14 +76,15 @@ struct MArgs {
 };
 
 // Shared-memory layout (byte offsets): the c / transform region for
-// instances with N <= Nsm, then two slot blocks sized for (Nsm, Kmax).
+// instances with N <= Nsm, which is also the stage tile of the instances with
+// N > 8192 when `tile` is set, then two slot blocks sized for (Nsm, Kmax).
 template <class E>
 struct MLayout {
   size_t regA, regA_n, slot[2], z, x, g, part, xw, lam, bits, kidx, slot_bytes, redC, rvC, rjC, total;
 };
 
 template <class E>
-__host__ __device__ inline MLayout<E> mlayout(int Nsm, int K, int path) {
+__host__ __device__ inline MLayout<E> mlayout(int Nsm, bool tile, int K, int path) {
   using W = typename FT<E>::W;
   using V = typename NormT<E>::V;
   MLayout<E> L;
@@ -99,6 +103,7 @@ __host__ __device__ inline MLayout<E> mlayout(int Nsm, int K, int path) {
   L.slot_bytes = o;
   size_t t = 0;
   L.regA_n = (size_t)((path != PATH_CONV && kernel_doubled<E>(Nsm)) ? 2 * Nsm : Nsm);
+  if (tile && L.regA_n < (size_t)kGTile) L.regA_n = kGTile;
   L.regA = t; t = a16(t + L.regA_n * sizeof(E));
   L.slot[0] = t; t += L.slot_bytes;
   L.slot[1] = t; t += L.slot_bytes;
@@ -192,9 +197,11 @@ __device__ void mcorr_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, 
     for (int i = g.tid; i < ((I.P.N + 31) >> 5); i += g.n) v.bits[i] = 0u;
     // t = 1: h_0 = Phi^H y by one transform, fused with step 3
     double yy[1] = {0.0};
-    const int l = correlate_transform<E, DFT, true>(g, v.buf, I.P, I.y, v.h0, yy, rv, rj);
+    const int l = (I.big && a.gtile)
+                      ? gcorrelate_transform<E, DFT>(g, v.buf, (E*)(sm + L.regA), I.P, I.y, v.h0, yy, rv, rj)
+                      : correlate_transform<E, DFT, true>(g, v.buf, I.P, I.y, v.h0, yy, rv, rj);
     group_sum(g, yy, red);
-    if (!I.big && g.tid == 0) ckey = nullptr;  // the shared region held the transform
+    if (g.tid == 0) ckey = nullptr;  // the shared region held the transform or its tiles
     if (!(yy[0] > 0.0) || I.K == 0) {
       mwrite(g, a, I, v, 0, yy[0], yy[0]);
       g.sync();
@@ -229,8 +236,10 @@ __device__ void mcorr_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, 
     }
     l = correlate_fast<E, DFT>(g, regA, v.h0, v.lam, v.xw, p, N, v.bits, nullptr, rv, rj, dbl);
   } else {
-    l = correlate_residual<E, DFT>(g, v.buf, I.P, I.y, v.bits, v.kidx, v.xw, rv, rj);
-    if (!I.big && g.tid == 0) ckey = nullptr;
+    l = (I.big && a.gtile)
+            ? gcorrelate_residual<E, DFT>(g, v.buf, (E*)(sm + L.regA), I.P, I.y, v.bits, v.kidx, v.xw, rv, rj)
+            : correlate_residual<E, DFT>(g, v.buf, I.P, I.y, v.bits, v.kidx, v.xw, rv, rj);
+    if (g.tid == 0) ckey = nullptr;
   }
   if (g.tid == 0) {
     S.lnew = l;
@@ -292,7 +301,7 @@ __global__ void __launch_bounds__(kMThreads, (sizeof(E) > 4 ? 1 : 2)) omp_multi_
   __shared__ MSlot<E> S[2];
   __shared__ const void* ckey;
   __shared__ LsShared<W> l_sh;
-  const MLayout<E> L = mlayout<E>(a.Nsm, a.Kmax, a.path);
+  const MLayout<E> L = mlayout<E>(a.Nsm, a.gtile != 0, a.Kmax, a.path);
   const bool isC = threadIdx.x < kCThreads;
   const Grp gC{(int)threadIdx.x, kCThreads, 1};
   const Grp gL{(int)threadIdx.x - kCThreads, kLThreads, 2};
@@ -350,9 +359,17 @@ Sizes sizes_of(const MultiItem* it, int64_t n) {
   return z;
 }
 
+// Shared memory of a launch: with the stage tile when the instances with
+// N > 8192 fit it beside the slots, else without (they then run the chains
+// pass by pass on their global vector).
 template <class E>
-size_t smem_t(const Sizes& z, int path) {
-  return mlayout<E>(z.Nsm, z.Kmax, path).total;
+size_t smem_t(const Sizes& z, int path, bool* tile) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t with = mlayout<E>(z.Nsm, z.Nbig > 0, z.Kmax, path).total;
+  *tile = z.Nbig > 0 && with <= (size_t)optin;
+  return *tile ? with : mlayout<E>(z.Nsm, false, z.Kmax, path).total;
 }
 
 template <class E>
@@ -361,13 +378,15 @@ cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int* ite
   using W = typename FT<E>::W;
   std::stable_sort(it, it + n, [](const MultiItem& u, const MultiItem& v) { return u.cost > v.cost; });
   const Sizes z = sizes_of(it, n);
-  const size_t smem = smem_t<E>(z, path);
-  cudaError_t e = raise_smem_limit((const void*)omp_multi_kernel<E>, smem);
+  bool tile = false;
+  const size_t smem = smem_t<E>(z, path, &tile);
+  const void* kfn = (const void*)omp_multi_kernel<E>;
+  cudaError_t e = raise_smem_limit(kfn, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, omp_multi_kernel<E>, kMThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kMThreads, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const int64_t need = (n + 1) / 2, cap = (int64_t)occ * sms;
@@ -402,6 +421,7 @@ cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int* ite
   a.path = path;
   a.Nsm = z.Nsm;
   a.Nbig = z.Nbig;
+  a.gtile = tile ? 1 : 0;
   a.Nmax = z.Nmax;
   a.Kmax = z.Kmax;
   a.iters_out = iters_out;
@@ -453,7 +473,7 @@ cudaError_t chain_twiddles(int logN, cudaStream_t st, const void** tw64, const v
   return cudaSuccess;
 }
 
-int multi_switch_big(int logN) { return logN <= kMaxLogN ? 64 : 16; }
+int multi_switch_big(int logN) { return logN <= kMaxLogN ? 64 : 32; }
 
 // Work of one instance in FMA-like units: the correlation (kernel sums up to
 // the switch, two transforms per iteration after it; global-memory buffers
@@ -470,8 +490,9 @@ double multi_cost(const PlanView& P, int K, int t_switch, int path) {
 size_t omp_multi_smem(const MultiItem* it, int64_t n, int path) {
   const Sizes z = sizes_of(it, n);
   const PlanView& P = *it[0].P;
-  if (P.dft) return P.fp32 ? smem_t<float2>(z, path) : smem_t<double2>(z, path);
-  return P.fp32 ? smem_t<float>(z, path) : smem_t<double>(z, path);
+  bool tile = false;
+  if (P.dft) return P.fp32 ? smem_t<float2>(z, path, &tile) : smem_t<double2>(z, path, &tile);
+  return P.fp32 ? smem_t<float>(z, path, &tile) : smem_t<double>(z, path, &tile);
 }
 
 cudaError_t launch_omp_multi(MultiItem* it, int64_t n, double rel_tol, int path, int* iters_out, double* res_out,
