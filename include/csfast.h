@@ -186,8 +186,11 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
  * own plan (own Omega, N, M, kind and precision) and their own K: an uneven
  * batch.  The instances of one element type (kind, precision) and residence
  * (N <= 8192 in shared memory, larger N in global memory) run in one
- * persistent kernel, two instances per CTA, taken longest first; the launches
- * run one after another on `stream`.  Instance b gets the
+ * persistent launch (two instances per CTA in shared memory, one per CTA and
+ * several CTAs per SM in global memory), instances taken longest first.
+ * With more than one launch, each runs on a stream the library owns, forked
+ * from `stream` and joined back into it by events (stream capture follows
+ * the fork).  Instance b gets the
  * outputs cs_omp gives for (plans[b], y_dev[b], K[b]):
  *   plans      host array [count] of plans on the current device (a plan may
  *              appear more than once); N <= 2^16; plans with N > 8192 need

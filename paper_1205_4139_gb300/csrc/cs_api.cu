@@ -1,5 +1,6 @@
 // C ABI of libcsfast.so (declared in include/csfast.h): argument checks,
 // plan tables, workspace management and launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -79,6 +80,24 @@ cudaError_t raise_smem_limit(const void* func, size_t bytes) {
   const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) cur = bytes;
   return e;
+}
+
+// Streams the library forks work onto (k < 8 per device), created on first
+// use and kept until the process exits.
+cudaError_t fork_stream(int dev, int k, cudaStream_t* out) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, cudaStream_t> pool;
+  std::lock_guard<std::mutex> lk(mu);
+  cudaStream_t& s = pool[std::make_pair(dev, k)];
+  if (!s) {
+    const cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      s = nullptr;
+      return e;
+    }
+  }
+  *out = s;
+  return cudaSuccess;
 }
 
 // accessors for the other translation units of the library
@@ -545,12 +564,42 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
     }
   }
   cudaStream_t st = (cudaStream_t)stream;
-  for (auto& g : group) {
-    if (g.empty()) continue;
+  // launches with the most work first; with several, each runs on a stream of
+  // its own forked from and joined back into `stream`, so that the CTAs of a
+  // later launch fill the SMs an earlier one leaves idle in its tail
+  std::vector<int> order;
+  std::vector<double> work(8, 0.0);
+  for (int gi = 0; gi < 8; ++gi) {
+    for (const MultiItem& it : group[gi]) work[gi] += it.cost;
+    if (!group[gi].empty()) order.push_back(gi);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return work[u] > work[v]; });
+  if (order.size() == 1) {
+    std::vector<MultiItem>& g = group[order[0]];
     CS_CUDA(launch_omp_multi(g.data(), (int64_t)g.size(), h.rel_tol, h.path, iters_dev, resnorm_dev,
                              plans[0]->v.status, st),
             "omp_batched kernel");
+    return CS_OK;
   }
+  cudaEvent_t fork = nullptr;
+  CS_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "omp_batched event");
+  cudaError_t e = cudaEventRecord(fork, st);
+  for (size_t k = 0; k < order.size() && e == cudaSuccess; ++k) {
+    std::vector<MultiItem>& g = group[order[k]];
+    cudaStream_t aux = nullptr;
+    cudaEvent_t done = nullptr;
+    e = fork_stream(dev, (int)k, &aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, fork, 0);
+    if (e == cudaSuccess)
+      e = launch_omp_multi(g.data(), (int64_t)g.size(), h.rel_tol, h.path, iters_dev, resnorm_dev,
+                           plans[0]->v.status, aux);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(done, aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, done, 0);
+    if (done) cudaEventDestroy(done);
+  }
+  cudaEventDestroy(fork);
+  CS_CUDA(e, "omp_batched kernels");
   return CS_OK;
 }
 

@@ -1,26 +1,26 @@
 // OMP (Algorithm 1.1) on a batch of instances that each bring their own
 // plan: their own row set Omega, N (up to 2^16), M and K.  One persistent
-// kernel per element type runs all instances of that type.
+// launch per element type and residence runs all instances of that kind, in
+// a list sorted by decreasing estimated work that the CTAs take from with an
+// atomic counter (the instances that start last are short ones).
 //
-// The structure is that of the batched kernel of cs_omp.cu: two instances
-// ("slots") per CTA, a correlation group of 8 warps (the initial transform,
-// then per iteration the kernel sums of Eq. kernelsumOMP or the transforms of
-// the zero-filled residual, fused with the identification of step 3) and a
-// least-squares group of 4 warps (the FP64 Cholesky append of step 6, the
-// residual downdate and the halting test of step 8) serving the two slots in
-// alternating phases.  What differs:
-//   * each slot carries its instance's descriptor (plan tables, y, K,
-//     outputs) in shared memory;
-//   * CTAs take instances from a list sorted by decreasing estimated work, so
-//     that the instances that start last are short ones;
-//   * c is staged in shared memory per plan, again whenever the correlation
-//     group turns to a slot of another plan;
-//   * instances with N > 8192 keep their transform vector, support bitmap and
-//     position map in global memory (one vector per CTA, the others per slot;
-//     they stay in L2 for the most part) and read c straight from the plan:
-//     their transforms are the same radix-16 chains, two passes per round
-//     trip through a shared-memory tile (cs_gchain.cuh), and their kernel
-//     sums stream c through L2.
+// Shared-memory residence (N <= 8192), omp_multi_kernel: the structure of
+// the batched kernel of cs_omp.cu, two instances ("slots") per CTA, a
+// correlation group of 8 warps (the initial transform, then per iteration
+// the kernel sums of Eq. kernelsumOMP or the transforms of the zero-filled
+// residual, fused with the identification of step 3) and a least-squares
+// group of 4 warps (the FP64 Cholesky append of step 6, the residual
+// downdate and the halting test of step 8) serving the two slots in
+// alternating phases.  Each slot carries its instance's descriptor (plan
+// tables, y, K, outputs) in shared memory, and c is staged again whenever
+// the correlation group turns to a slot of another plan.
+//
+// Global-memory residence (8192 < N <= 2^16), omp_seq_kernel: one instance
+// per CTA at a time and several CTAs per SM; the transform vector, support
+// bitmap and position map live in a global workspace (mostly in L2), c is
+// read straight from the plan, and the transforms are the same radix-16
+// chains, two passes per round trip through a shared-memory tile
+// (cs_gchain.cuh).
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -50,7 +50,7 @@ struct MInst {
   const E* y;               // [M]
   typename FT<E>::W* x;     // [K] FP64 coefficients (nullable)
   int* supp;                // [K]
-  int K, t_switch, idx, big;  // big: buffers in global memory (N > 8192)
+  int K, t_switch, idx, pad;
 };
 
 template <class E>
@@ -59,32 +59,30 @@ struct MArgs {
   int64_t count;
   double rel_tol;
   int path;
-  int Nsm;    // largest N of the instances kept in shared memory (0: none)
-  int Nbig;   // largest N of the instances kept in global memory (0: none)
-  int gtile;  // 1: those instances transform through a shared-memory stage tile
+  int Nsm;    // largest N of a shared-memory launch (0 in a global-memory one)
+  int Nbig;   // largest N of a global-memory launch (0 in a shared-memory one)
   int Nmax, Kmax;
   int* iters_out;             // [count], by instance index (nullable)
   double* res_out;            // [count] (nullable)
   E* h0_ws;                   // [grid][2][Nmax]
   typename FT<E>::W* B_ws;    // [grid][2][Kmax(Kmax+1)/2]
-  E* buf_ws;                  // [grid][Nbig] transform buffer
-  uint32_t* bits_ws;          // [grid][2][Nbig/32]
-  uint16_t* kidx_ws;          // [grid][2][Nbig]
+  E* buf_ws;                  // global-memory launches: [grid][Nbig] transform vector
+  uint32_t* bits_ws;          //   [grid][Nbig/32] support bitmap
+  uint16_t* kidx_ws;          //   [grid][Nbig] position -> index in the support
   int* counter;
   int* status;
   long long max_phases;
 };
 
-// Shared-memory layout (byte offsets): the c / transform region for
-// instances with N <= Nsm, which is also the stage tile of the instances with
-// N > 8192 when `tile` is set, then two slot blocks sized for (Nsm, Kmax).
+// Shared-memory layout of omp_multi_kernel (byte offsets): the c / transform
+// region, then two slot blocks sized for (Nsm, Kmax).
 template <class E>
 struct MLayout {
   size_t regA, regA_n, slot[2], z, x, g, part, xw, lam, bits, kidx, slot_bytes, redC, rvC, rjC, total;
 };
 
 template <class E>
-__host__ __device__ inline MLayout<E> mlayout(int Nsm, bool tile, int K, int path) {
+__host__ __device__ inline MLayout<E> mlayout(int Nsm, int K, int path) {
   using W = typename FT<E>::W;
   using V = typename NormT<E>::V;
   MLayout<E> L;
@@ -103,7 +101,6 @@ __host__ __device__ inline MLayout<E> mlayout(int Nsm, bool tile, int K, int pat
   L.slot_bytes = o;
   size_t t = 0;
   L.regA_n = (size_t)((path != PATH_CONV && kernel_doubled<E>(Nsm)) ? 2 * Nsm : Nsm);
-  if (tile && L.regA_n < (size_t)kGTile) L.regA_n = kGTile;
   L.regA = t; t = a16(t + L.regA_n * sizeof(E));
   L.slot[0] = t; t += L.slot_bytes;
   L.slot[1] = t; t += L.slot_bytes;
@@ -136,8 +133,7 @@ struct MView {
 };
 
 template <class E>
-__device__ __forceinline__ MView<E> mview(unsigned char* sm, const MLayout<E>& L, int s, const MArgs<E>& a,
-                                          bool big) {
+__device__ __forceinline__ MView<E> mview(unsigned char* sm, const MLayout<E>& L, int s, const MArgs<E>& a) {
   using W = typename FT<E>::W;
   MView<E> v;
   unsigned char* base = sm + L.slot[s];
@@ -148,11 +144,11 @@ __device__ __forceinline__ MView<E> mview(unsigned char* sm, const MLayout<E>& L
   v.xw = (E*)(base + L.xw);
   v.lam = (int*)(base + L.lam);
   const size_t ls = (size_t)blockIdx.x * 2 + s;
-  v.bits = big ? a.bits_ws + ls * (size_t)(a.Nbig >> 5) : (uint32_t*)(base + L.bits);
-  v.kidx = big ? a.kidx_ws + ls * (size_t)a.Nbig : (uint16_t*)(base + L.kidx);
+  v.bits = (uint32_t*)(base + L.bits);
+  v.kidx = (uint16_t*)(base + L.kidx);
   v.h0 = a.h0_ws + ls * (size_t)a.Nmax;
   v.B = a.B_ws + ls * tri(a.Kmax);
-  v.buf = big ? a.buf_ws + (size_t)blockIdx.x * a.Nbig : (E*)(sm + L.regA);
+  v.buf = (E*)(sm + L.regA);
   return v;
 }
 
@@ -193,15 +189,13 @@ __device__ void mcorr_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, 
     if (g.tid == 0) S.I = a.inst[b];
     g.sync();
     const MInst<E>& I = S.I;
-    const MView<E> v = mview(sm, L, s, a, I.big != 0);
+    const MView<E> v = mview(sm, L, s, a);
     for (int i = g.tid; i < ((I.P.N + 31) >> 5); i += g.n) v.bits[i] = 0u;
     // t = 1: h_0 = Phi^H y by one transform, fused with step 3
     double yy[1] = {0.0};
-    const int l = (I.big && a.gtile)
-                      ? gcorrelate_transform<E, DFT>(g, v.buf, (E*)(sm + L.regA), I.P, I.y, v.h0, yy, rv, rj)
-                      : correlate_transform<E, DFT, true>(g, v.buf, I.P, I.y, v.h0, yy, rv, rj);
+    const int l = correlate_transform<E, DFT, true>(g, v.buf, I.P, I.y, v.h0, yy, rv, rj);
     group_sum(g, yy, red);
-    if (g.tid == 0) ckey = nullptr;  // the shared region held the transform or its tiles
+    if (g.tid == 0) ckey = nullptr;  // the shared region held the transform
     if (!(yy[0] > 0.0) || I.K == 0) {
       mwrite(g, a, I, v, 0, yy[0], yy[0]);
       g.sync();
@@ -219,14 +213,11 @@ __device__ void mcorr_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, 
   }
   if (S.state != NEED_CORR) return;
   const MInst<E>& I = S.I;
-  const MView<E> v = mview(sm, L, s, a, I.big != 0);
+  const MView<E> v = mview(sm, L, s, a);
   const int p = S.p, t = p + 1, N = I.P.N;
   const bool fast = a.path == PATH_FAST || (a.path == PATH_HYBRID && t <= I.t_switch);
   int l;
-  if (fast && I.big) {
-    // c straight from the plan (full storage, working precision)
-    l = correlate_fast<E, DFT>(g, I.P.c, v.h0, v.lam, v.xw, p, N, v.bits, nullptr, rv, rj, false);
-  } else if (fast) {
+  if (fast) {
     E* regA = (E*)(sm + L.regA);
     const bool dbl = DFT && kernel_doubled<E>(N) && 2 * (size_t)N <= L.regA_n;
     const void* key = c_key(I.P);
@@ -236,9 +227,7 @@ __device__ void mcorr_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, 
     }
     l = correlate_fast<E, DFT>(g, regA, v.h0, v.lam, v.xw, p, N, v.bits, nullptr, rv, rj, dbl);
   } else {
-    l = (I.big && a.gtile)
-            ? gcorrelate_residual<E, DFT>(g, v.buf, (E*)(sm + L.regA), I.P, I.y, v.bits, v.kidx, v.xw, rv, rj)
-            : correlate_residual<E, DFT>(g, v.buf, I.P, I.y, v.bits, v.kidx, v.xw, rv, rj);
+    l = correlate_residual<E, DFT>(g, v.buf, I.P, I.y, v.bits, v.kidx, v.xw, rv, rj);
     if (g.tid == 0) ckey = nullptr;
   }
   if (g.tid == 0) {
@@ -253,7 +242,7 @@ __device__ void mls_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, un
                          LsShared<typename FT<E>::W>& sh) {
   if (S.state != NEED_LS) return;
   const MInst<E>& I = S.I;
-  const MView<E> v = mview(sm, L, s, a, I.big != 0);
+  const MView<E> v = mview(sm, L, s, a);
   const int K = I.K, p = S.p, l = S.lnew;
   const double ynorm2 = S.ynorm2;
   if (l < 0) {  // no candidate column left
@@ -301,7 +290,7 @@ __global__ void __launch_bounds__(kMThreads, (sizeof(E) > 4 ? 1 : 2)) omp_multi_
   __shared__ MSlot<E> S[2];
   __shared__ const void* ckey;
   __shared__ LsShared<W> l_sh;
-  const MLayout<E> L = mlayout<E>(a.Nsm, a.gtile != 0, a.Kmax, a.path);
+  const MLayout<E> L = mlayout<E>(a.Nsm, a.Kmax, a.path);
   const bool isC = threadIdx.x < kCThreads;
   const Grp gC{(int)threadIdx.x, kCThreads, 1};
   const Grp gL{(int)threadIdx.x - kCThreads, kLThreads, 2};
@@ -327,6 +316,120 @@ __global__ void __launch_bounds__(kMThreads, (sizeof(E) > 4 ? 1 : 2)) omp_multi_
       mcorr_step<E>(gC, a, S[sc], sc, sm, L, (double*)(sm + L.redC), (V*)(sm + L.rvC), (int*)(sm + L.rjC), ckey);
     } else {
       mls_step<E>(gL, a, S[sc ^ 1], sc ^ 1, sm, L, l_sh);
+    }
+  }
+}
+
+// ------------------------------------------------ global-memory residence
+// One instance per CTA at a time, its 8 warps running the correlation and
+// the least squares of each iteration in turn, several CTAs per SM.  These
+// instances are bound by the latency of their round trips through L2, not by
+// a pipe, so several independent instances per SM hide one another's waits
+// better than one CTA whose warp groups alternate between two instances
+// (measured: 151 ms against 183 ms for 1221 complex instances).
+constexpr int kSThreads = 256;
+
+template <class E>
+constexpr int seq_min_blocks() {
+  return sizeof(E) == 4 ? 4 : (sizeof(E) == 8 ? 3 : 2);
+}
+
+template <class E>
+struct SLayout {
+  size_t tile, z, x, g, part, xw, lam, red, rv, rj, total;
+};
+
+template <class E>
+__host__ __device__ inline SLayout<E> slayout(int K) {
+  using W = typename FT<E>::W;
+  using V = typename NormT<E>::V;
+  SLayout<E> L;
+  const int Kc = K > 0 ? K : 1;
+  const int npart = (2 * kSThreads > Kc ? 2 * kSThreads : Kc) +
+                    (3 * Kc * (int)sizeof(double) + (int)sizeof(W) - 1) / (int)sizeof(W);
+  size_t o = 0;
+  L.tile = o; o = a16(o + (size_t)kGTile * sizeof(E));
+  L.z = o;    o = a16(o + (size_t)Kc * sizeof(W));
+  L.x = o;    o = a16(o + (size_t)Kc * sizeof(W));
+  L.g = o;    o = a16(o + (size_t)Kc * sizeof(W));
+  L.part = o; o = a16(o + (size_t)npart * sizeof(W));
+  L.xw = o;   o = a16(o + (size_t)Kc * sizeof(E));
+  L.lam = o;  o = a16(o + (size_t)Kc * sizeof(int));
+  L.red = o;  o = a16(o + (size_t)(32 * 4 + 4) * sizeof(double));
+  L.rv = o;   o = a16(o + 34 * sizeof(V));
+  L.rj = o;   o = a16(o + 34 * sizeof(int));
+  L.total = o;
+  return L;
+}
+
+template <class E>
+__global__ void __launch_bounds__(kSThreads, seq_min_blocks<E>()) omp_seq_kernel(MArgs<E> a) {
+  using W = typename FT<E>::W;
+  using V = typename NormT<E>::V;
+  constexpr bool DFT = FT<E>::C;
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ MInst<E> I;
+  __shared__ long long b_s;
+  __shared__ double rn2;
+  __shared__ LsShared<W> sh;
+  const SLayout<E> L = slayout<E>(a.Kmax);
+  const Grp g = whole_block();
+  E* tile = (E*)(sm + L.tile);
+  double* red = (double*)(sm + L.red);
+  V* rv = (V*)(sm + L.rv);
+  int* rj = (int*)(sm + L.rj);
+  const size_t cta = blockIdx.x;
+  LsView<E> lv;
+  lv.B = a.B_ws + cta * tri(a.Kmax);
+  lv.z = (W*)(sm + L.z);
+  lv.x = (W*)(sm + L.x);
+  lv.g = (W*)(sm + L.g);
+  lv.part = (W*)(sm + L.part);
+  lv.terms = (double*)(lv.part + (2 * kSThreads > a.Kmax ? 2 * kSThreads : a.Kmax));
+  lv.xw = (E*)(sm + L.xw);
+  lv.lam = (int*)(sm + L.lam);
+  lv.bits = a.bits_ws + cta * (size_t)(a.Nbig >> 5);
+  lv.kidx = a.kidx_ws + cta * (size_t)a.Nbig;
+  E* h0 = a.h0_ws + cta * (size_t)a.Nmax;
+  E* buf = a.buf_ws + cta * (size_t)a.Nbig;
+  // a CTA serves each instance at most once; the bound only guards the loop
+  for (int64_t served = 0; served <= a.count; ++served) {
+    __syncthreads();  // every thread is done with the previous descriptor
+    if (g.tid == 0) {
+      b_s = atomicAdd(a.counter, 1);
+      if (b_s < a.count) I = a.inst[b_s];
+    }
+    __syncthreads();
+    if (b_s >= a.count) break;
+    const int N = I.P.N, K = I.K;
+    for (int i = g.tid; i < ((N + 31) >> 5); i += g.n) lv.bits[i] = 0u;
+    // t = 1: h_0 = Phi^H y by one transform, fused with step 3
+    double yy[1] = {0.0};
+    int l = gcorrelate_transform<E, DFT>(g, buf, tile, I.P, I.y, h0, yy, rv, rj);
+    group_sum(g, yy, red);
+    const double ynorm2 = yy[0];
+    if (g.tid == 0) rn2 = ynorm2;
+    g.sync();
+    int p = 0;
+    if (ynorm2 > 0.0 && K > 0) {
+      for (;;) {
+        if (l < 0) break;                                   // no candidate column left
+        ls_append(g, I.P, lv, h0, p, l, rn2, sh);            // step 6
+        if (sh.st == 1) break;                              // column dependent on Lambda
+        ++p;
+        if (p >= K || rn2 < a.rel_tol * a.rel_tol * ynorm2) break;  // step 8
+        const bool fast = a.path == PATH_FAST || (a.path == PATH_HYBRID && p + 1 <= I.t_switch);
+        l = fast ? correlate_fast<E, DFT>(g, I.P.c, h0, lv.lam, lv.xw, p, N, lv.bits, nullptr, rv, rj, false)
+                 : gcorrelate_residual<E, DFT>(g, buf, tile, I.P, I.y, lv.bits, lv.kidx, lv.xw, rv, rj);
+      }
+    }
+    for (int k = g.tid; k < K; k += g.n) {
+      if (I.x) I.x[k] = k < p ? lv.x[k] : W{};
+      I.supp[k] = k < p ? lv.lam[k] : -1;
+    }
+    if (g.tid == 0) {
+      if (a.iters_out) a.iters_out[I.idx] = p;
+      if (a.res_out) a.res_out[I.idx] = ynorm2 > 0.0 ? sqrt(fmax(rn2, 0.0) / ynorm2) : 0.0;
     }
   }
 }
@@ -359,17 +462,10 @@ Sizes sizes_of(const MultiItem* it, int64_t n) {
   return z;
 }
 
-// Shared memory of a launch: with the stage tile when the instances with
-// N > 8192 fit it beside the slots, else without (they then run the chains
-// pass by pass on their global vector).
+// Shared memory of a launch of one residence.
 template <class E>
-size_t smem_t(const Sizes& z, int path, bool* tile) {
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t with = mlayout<E>(z.Nsm, z.Nbig > 0, z.Kmax, path).total;
-  *tile = z.Nbig > 0 && with <= (size_t)optin;
-  return *tile ? with : mlayout<E>(z.Nsm, false, z.Kmax, path).total;
+size_t smem_t(const Sizes& z, int path) {
+  return z.Nsm == 0 ? slayout<E>(z.Kmax).total : mlayout<E>(z.Nsm, z.Kmax, path).total;
 }
 
 template <class E>
@@ -378,19 +474,22 @@ cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int* ite
   using W = typename FT<E>::W;
   std::stable_sort(it, it + n, [](const MultiItem& u, const MultiItem& v) { return u.cost > v.cost; });
   const Sizes z = sizes_of(it, n);
-  bool tile = false;
-  const size_t smem = smem_t<E>(z, path, &tile);
-  const void* kfn = (const void*)omp_multi_kernel<E>;
+  if (z.Nsm > 0 && z.Nbig > 0) return cudaErrorInvalidValue;  // one residence per launch
+  const bool seq = z.Nsm == 0;  // global-memory residence
+  const size_t smem = smem_t<E>(z, path);
+  const void* kfn = seq ? (const void*)omp_seq_kernel<E> : (const void*)omp_multi_kernel<E>;
+  const int threads = seq ? kSThreads : kMThreads;
   cudaError_t e = raise_smem_limit(kfn, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kMThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, threads, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  const int64_t need = (n + 1) / 2, cap = (int64_t)occ * sms;
+  const int64_t need = seq ? n : (n + 1) / 2, cap = (int64_t)occ * sms;
   const int grid = (int)(need < cap ? need : cap);
+  const int per = seq ? 1 : 2;  // instance slots per CTA
 
   std::vector<MInst<E>> d((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
@@ -402,10 +501,11 @@ cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int* ite
     m.K = it[i].K;
     m.t_switch = it[i].t_switch;
     m.idx = it[i].idx;
-    m.big = it[i].P->large ? 1 : 0;
+    m.pad = 0;
   }
-  // workspace, stream-ordered: counter | descriptors | h0 | B | buffer | bits | kidx
-  const size_t g2 = (size_t)grid * 2;
+  // workspace, stream-ordered: counter | descriptors | h0 | B | vector | bits | kidx
+  // (the last three in global-memory launches only: Nbig = 0 otherwise)
+  const size_t g2 = (size_t)grid * per;
   const size_t o_inst = 16, o_h0 = a16(o_inst + (size_t)n * sizeof(MInst<E>));
   const size_t o_B = a16(o_h0 + g2 * z.Nmax * sizeof(E));
   const size_t o_buf = a16(o_B + g2 * tri(z.Kmax) * sizeof(W));
@@ -421,7 +521,6 @@ cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int* ite
   a.path = path;
   a.Nsm = z.Nsm;
   a.Nbig = z.Nbig;
-  a.gtile = tile ? 1 : 0;
   a.Nmax = z.Nmax;
   a.Kmax = z.Kmax;
   a.iters_out = iters_out;
@@ -438,7 +537,8 @@ cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int* ite
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ws + o_inst, d.data(), (size_t)n * sizeof(MInst<E>), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
-    omp_multi_kernel<E><<<grid, kMThreads, smem, st>>>(a);
+    if (seq) omp_seq_kernel<E><<<grid, kSThreads, smem, st>>>(a);
+    else omp_multi_kernel<E><<<grid, kMThreads, smem, st>>>(a);
     e = cudaGetLastError();
   }
   const cudaError_t e2 = cudaFreeAsync(ws, st);
@@ -490,9 +590,8 @@ double multi_cost(const PlanView& P, int K, int t_switch, int path) {
 size_t omp_multi_smem(const MultiItem* it, int64_t n, int path) {
   const Sizes z = sizes_of(it, n);
   const PlanView& P = *it[0].P;
-  bool tile = false;
-  if (P.dft) return P.fp32 ? smem_t<float2>(z, path, &tile) : smem_t<double2>(z, path, &tile);
-  return P.fp32 ? smem_t<float>(z, path, &tile) : smem_t<double>(z, path, &tile);
+  if (P.dft) return P.fp32 ? smem_t<float2>(z, path) : smem_t<double2>(z, path);
+  return P.fp32 ? smem_t<float>(z, path) : smem_t<double>(z, path);
 }
 
 cudaError_t launch_omp_multi(MultiItem* it, int64_t n, double rel_tol, int path, int* iters_out, double* res_out,
