@@ -2,10 +2,14 @@
 partial-DFT complex64 workload (N=4096, M=1024, K=64, 40 dB), then one
 cs_correlate launch: the case the committed ncu summaries capture.  With
 `single`, the same launches on the one partial-WHT FP64 instance (N=1024,
-M=256, K=16, noiseless) of the latency measurement.
+M=256, K=16, noiseless) of the latency measurement.  With `uneven`, the
+first `count` instances of one kind (wht / dft / all) and residence (small:
+N <= 8192, big: larger N, all) of the 4096-instance uneven batch, in two
+cs_omp_batched calls (the second is the one to capture).
 
   python -m paper_1205_4139_gb300.profile_case [batch]
   python -m paper_1205_4139_gb300.profile_case 1 single
+  python -m paper_1205_4139_gb300.profile_case uneven dft big 304
 """
 import os
 import sys
@@ -15,12 +19,38 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def uneven(kind, residence, count):
+    import torch
+
+    import synth
+    from paper_1205_4139_gb300 import binding
+
+    def keep(s):
+        return (kind == "all" or s["kind"] == kind) and (residence == "all" or (s["N"] > 8192) == (residence == "big"))
+
+    specs = [s for s in synth.uneven_batch(4096, seed=0) if keep(s)][:count]
+    plans, ys = [], []
+    for sp in specs:
+        om, yv = synth.uneven_instance(sp)
+        plans.append(binding.Plan(sp["N"], om, sp["kind"], "fp32"))
+        ys.append(torch.from_numpy(yv).cuda())
+    bt = binding.Batch(plans, ys, [sp["K"] for sp in specs])
+    for _ in range(2):
+        bt.run()
+    torch.cuda.synchronize()
+    assert plans[0].device_error() == 0
+    print("ok", len(specs), int(bt.iters.sum()))
+
+
 def main():
     import torch
 
     import synth
     from paper_1205_4139_gb300 import binding
 
+    if len(sys.argv) > 1 and sys.argv[1] == "uneven":
+        uneven(sys.argv[2], sys.argv[3], int(sys.argv[4]))
+        return
     B = int(sys.argv[1]) if len(sys.argv) > 1 else 456
     single = len(sys.argv) > 2 and sys.argv[2] == "single"
     cfg = dict(synth.CONFIG_WHT_FP64_SINGLE if single else synth.CONFIG_DFT_C64_BATCH)
