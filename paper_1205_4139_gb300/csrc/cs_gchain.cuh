@@ -8,6 +8,13 @@
 // the chain's first / last pass fuse the zero-fill of a measurement and the
 // masked residual of Algorithm 1.1 step 7 into it.
 //
+// Twiddles of passes 0 and 1 (W_N^e, e < N) would be read from a table as
+// long as the vector; instead they are W_N^(256 hi) W_N^lo, e = 256 hi + lo,
+// from two 256-entry tables in shared memory (`tws`, filled once per vector
+// by fill_split_twiddles): one more complex product per twiddle, and no
+// global-memory load.  Passes 2 and 3 use the chain's table (at most 256
+// entries of it, which stay in L1).
+//
 // KIND 0: forward DIF chain (natural order in, chain positions out);
 // KIND 1: adjoint DIT chain (chain positions in, natural order out);
 // KIND 2: Sylvester Walsh-Hadamard transform (natural order in and out,
@@ -62,6 +69,33 @@ struct ResidualSink {
   }
 };
 
+// exp(-2 pi i e / N) in the working precision (sincospi of an exact
+// argument: N is a power of two).
+template <class E>
+__device__ __forceinline__ E unit_root(int e, int N);
+template <>
+__device__ __forceinline__ float2 unit_root<float2>(int e, int N) {
+  float sn, cs;
+  sincospif(-2.0f * (float)e / (float)N, &sn, &cs);
+  return make_float2(cs, sn);
+}
+template <>
+__device__ __forceinline__ double2 unit_root<double2>(int e, int N) {
+  double sn, cs;
+  sincospi(-2.0 * (double)e / (double)N, &sn, &cs);
+  return make_double2(cs, sn);
+}
+
+// tws[i] = W_N^i and tws[256 + i] = W_N^(256 i), i < 256 (DFT only).
+template <class E>
+__device__ void fill_split_twiddles(const Grp& g, E* tws, int N) {
+  for (int i = g.tid; i < 256; i += g.n) {
+    tws[i] = unit_root<E>(i, N);
+    tws[256 + i] = unit_root<E>((256 * i) & (N - 1), N);
+  }
+  g.sync();
+}
+
 // Moves kGTile elements between a global vector and the tile: dst(i) =
 // src(i) for i < kGTile, every thread issuing 8 loads before its 8 stores so
 // that the loads overlap (one CTA per SM leaves little else to hide their
@@ -92,14 +126,11 @@ __device__ __forceinline__ void tile_move(const Grp& g, const SRC& src, const DS
 // m = 16 v + r.  DIF and WHT run pass 0 then pass 1 and take the loader;
 // DIT runs pass 1 then pass 0 and feeds the sink.
 template <int KIND, class E, class LD, class SK>
-__device__ void gstage_strided(const Grp& g, E* gbuf, E* tile, int logN, const E* __restrict__ tw, const LD& ld,
-                               SK& sk) {
+__device__ void gstage_strided(const Grp& g, E* gbuf, E* tile, int logN, const E* tws, const LD& ld, SK& sk) {
   constexpr bool hasLD = !std::is_same<LD, NoLoad>::value;
   constexpr bool hasSK = !std::is_same<SK, NoSink>::value;
   static_assert(!(hasLD && KIND == 1) && !(hasSK && KIND != 1), "loader / sink on the wrong stage");
-  const int N = 1 << logN, S1 = N >> 8, S0 = N >> 4;
-  const E* tw0 = tw;                                     // pass 0: L = N, table offset N - L = 0
-  const E* tw1 = KIND == 2 ? tw : tw + (N - (N >> 4));  // pass 1: L = N / 16 (no table for WHT)
+  const int N = 1 << logN, S1 = N >> 8;
   for (int c0 = 0; c0 < S1; c0 += 16) {
     if constexpr (!hasLD) {
       tile_move<E>(g, [&](int i) { return gbuf[c0 + (i & 15) + (i >> 4) * S1]; },
@@ -118,22 +149,26 @@ __device__ void gstage_strided(const Grp& g, E* gbuf, E* tile, int logN, const E
           if constexpr (hasLD) v[r] = outer ? ld(c + m * S1) : tile[16 * m + gg];
           else v[r] = tile[16 * m + gg];
         }
-        // butterfly index n within its sub-transform, and the pass's stride
-        const int n = outer ? c + w * S1 : c;
-        const int S = outer ? S0 : S1;
-        const E* t = outer ? tw0 : tw1;
+        // output / input q of this butterfly carries W_N^(q e1): pass 0
+        // (L = N) has W_N^(n q), n = c + w S1 its index within the
+        // transform; pass 1 (L = N/16) has W_{N/16}^(c q) = W_N^(16 c q)
+        const int e1 = outer ? c + w * S1 : 16 * c;
         if constexpr (KIND == 0) {
           dft_reg<16, -1>(v);
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             E o = v[bitrevc(q, 4)];
-            if (q > 0 && S > 1) o = mul(o, ldt(t + (q - 1) * S + n));
+            if (q > 0) {
+              const int e = q * e1;
+              o = mul(o, mul(tws[256 + (e >> 8)], tws[e & 255]));
+            }
             tile[16 * (m0 + q * mst) + gg] = o;
           }
         } else if constexpr (KIND == 1) {
-          if (S > 1) {
 #pragma unroll
-            for (int q = 1; q < 16; ++q) v[q] = mulc(v[q], ldt(t + (q - 1) * S + n));
+          for (int q = 1; q < 16; ++q) {
+            const int e = q * e1;
+            v[q] = mulc(v[q], mul(tws[256 + (e >> 8)], tws[e & 255]));
           }
           dft_reg<16, +1>(v);
 #pragma unroll
@@ -215,16 +250,17 @@ __device__ void gstage_contig(const Grp& g, E* gbuf, E* tile, int logN, const E*
 }
 
 // Whole chain of the kind on gbuf (natural positions; the caller's group
-// holds the tile).  `ld` feeds the chain's first pass, `sk` its last.
+// holds the tile).  `ld` feeds the chain's first pass, `sk` its last; tw is
+// the chain's twiddle table, tws the split tables of passes 0 and 1.
 template <int KIND, class E, class LD, class SK>
-__device__ void gchain(const Grp& g, E* gbuf, E* tile, int logN, const E* tw, const LD& ld, SK& sk) {
+__device__ void gchain(const Grp& g, E* gbuf, E* tile, int logN, const E* tw, const E* tws, const LD& ld, SK& sk) {
   NoLoad nl;
   NoSink ns;
   if constexpr (KIND == 1) {
     gstage_contig<1>(g, gbuf, tile, logN, tw, ld, ns);
-    gstage_strided<1>(g, gbuf, tile, logN, tw, nl, sk);
+    gstage_strided<1>(g, gbuf, tile, logN, tws, nl, sk);
   } else {
-    gstage_strided<KIND>(g, gbuf, tile, logN, tw, ld, ns);
+    gstage_strided<KIND>(g, gbuf, tile, logN, tws, ld, ns);
     gstage_contig<KIND>(g, gbuf, tile, logN, tw, nl, sk);
   }
 }
@@ -233,8 +269,9 @@ __device__ void gchain(const Grp& g, E* gbuf, E* tile, int logN, const E* tw, co
 // with the arg-max of step 3 and an optional store of h; *norm receives this
 // thread's share of sum |v_m|^2 (FP64).
 template <class E, bool DFT>
-__device__ int gcorrelate_transform(const Grp& g, E* gbuf, E* tile, const PlanDev<E>& P, const E* __restrict__ v,
-                                    E* h_out, double* norm, typename NormT<E>::V* rv, int* rj) {
+__device__ int gcorrelate_transform(const Grp& g, E* gbuf, E* tile, const E* tws, const PlanDev<E>& P,
+                                    const E* __restrict__ v, E* h_out, double* norm, typename NormT<E>::V* rv,
+                                    int* rj) {
   using R = typename FT<E>::R;
   using V = typename NormT<E>::V;
   double s = 0.0;
@@ -242,7 +279,7 @@ __device__ int gcorrelate_transform(const Grp& g, E* gbuf, E* tile, const PlanDe
   *norm = s;
   const ZeroFillLoad<E> ld{P.slot, v, inv_sqrt_pow2<R>(P.logN)};
   ArgmaxSink<E> sk{nullptr, h_out, (V)-1, 0x7fffffff, nullptr};
-  gchain<DFT ? 1 : 2>(g, gbuf, tile, P.logN, P.tw, ld, sk);
+  gchain<DFT ? 1 : 2>(g, gbuf, tile, P.logN, P.tw, tws, ld, sk);
   return group_argmax(g, sk.bv, sk.bj, rv, rj);
 }
 
@@ -251,17 +288,18 @@ __device__ int gcorrelate_transform(const Grp& g, E* gbuf, E* tile, const PlanDe
 // stage writes the masked residual, adjoint chain whose last stage feeds the
 // arg-max over j not in Lambda.
 template <class E, bool DFT>
-__device__ int gcorrelate_residual(const Grp& g, E* gbuf, E* tile, const PlanDev<E>& P, const E* __restrict__ y,
+__device__ int gcorrelate_residual(const Grp& g, E* gbuf, E* tile, const E* tws, const PlanDev<E>& P,
+                                   const E* __restrict__ y,
                                    const uint32_t* bits, const uint16_t* kidx, const E* xw,
                                    typename NormT<E>::V* rv, int* rj) {
   using R = typename FT<E>::R;
   using V = typename NormT<E>::V;
   const SparseLoader<E> sl{bits, kidx, xw};
   ResidualSink<E> rs{P.slot, y, inv_sqrt_pow2<R>(P.logN), (R)1 / (R)P.N, gbuf};
-  gchain<DFT ? 0 : 2>(g, gbuf, tile, P.logN, P.tw, sl, rs);
+  gchain<DFT ? 0 : 2>(g, gbuf, tile, P.logN, P.tw, tws, sl, rs);
   NoLoad nl;
   ArgmaxSink<E> sk{bits, nullptr, (V)-1, 0x7fffffff, nullptr};
-  gchain<DFT ? 1 : 2>(g, gbuf, tile, P.logN, P.tw, nl, sk);
+  gchain<DFT ? 1 : 2>(g, gbuf, tile, P.logN, P.tw, tws, nl, sk);
   return group_argmax(g, sk.bv, sk.bj, rv, rj);
 }
 

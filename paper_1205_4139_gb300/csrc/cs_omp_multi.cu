@@ -337,7 +337,7 @@ constexpr int seq_min_blocks() {
 
 template <class E>
 struct SLayout {
-  size_t tile, z, x, g, part, xw, lam, red, rv, rj, total;
+  size_t tile, tws, z, x, g, part, xw, lam, red, rv, rj, total;
 };
 
 // The least-squares scratch (g, part) is dead outside the least squares and
@@ -362,6 +362,7 @@ __host__ __device__ inline SLayout<E> slayout(int K) {
     L.g = o;    o = a16(o + (size_t)Kc * sizeof(W));
     L.part = o; o = a16(o + (size_t)npart * sizeof(W));
   }
+  L.tws = o;  o = a16(o + (FT<E>::C ? 512 : 0) * sizeof(E));  // split twiddle tables (DFT)
   L.z = o;    o = a16(o + (size_t)Kc * sizeof(W));
   L.x = o;    o = a16(o + (size_t)Kc * sizeof(W));
   L.xw = o;   o = a16(o + (size_t)Kc * sizeof(E));
@@ -386,6 +387,7 @@ __global__ void __launch_bounds__(kSThreads, seq_min_blocks<E>()) omp_seq_kernel
   const SLayout<E> L = slayout<E>(a.Kmax);
   const Grp g = whole_block();
   E* tile = (E*)(sm + L.tile);
+  E* tws = (E*)(sm + L.tws);
   double* red = (double*)(sm + L.red);
   V* rv = (V*)(sm + L.rv);
   int* rj = (int*)(sm + L.rj);
@@ -414,9 +416,10 @@ __global__ void __launch_bounds__(kSThreads, seq_min_blocks<E>()) omp_seq_kernel
     if (b_s >= a.count) break;
     const int N = I.P.N, K = I.K;
     for (int i = g.tid; i < ((N + 31) >> 5); i += g.n) lv.bits[i] = 0u;
+    if constexpr (DFT) fill_split_twiddles(g, tws, N);
     // t = 1: h_0 = Phi^H y by one transform, fused with step 3
     double yy[1] = {0.0};
-    int l = gcorrelate_transform<E, DFT>(g, buf, tile, I.P, I.y, h0, yy, rv, rj);
+    int l = gcorrelate_transform<E, DFT>(g, buf, tile, tws, I.P, I.y, h0, yy, rv, rj);
     group_sum(g, yy, red);
     const double ynorm2 = yy[0];
     if (g.tid == 0) rn2 = ynorm2;
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(kSThreads, seq_min_blocks<E>()) omp_seq_kernel
         if (p >= K || rn2 < a.rel_tol * a.rel_tol * ynorm2) break;  // step 8
         const bool fast = a.path == PATH_FAST || (a.path == PATH_HYBRID && p + 1 <= I.t_switch);
         l = fast ? correlate_fast<E, DFT>(g, I.P.c, h0, lv.lam, lv.xw, p, N, lv.bits, nullptr, rv, rj, false)
-                 : gcorrelate_residual<E, DFT>(g, buf, tile, I.P, I.y, lv.bits, lv.kidx, lv.xw, rv, rj);
+                 : gcorrelate_residual<E, DFT>(g, buf, tile, tws, I.P, I.y, lv.bits, lv.kidx, lv.xw, rv, rj);
       }
     }
     for (int k = g.tid; k < K; k += g.n) {
