@@ -189,8 +189,9 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
  * persistent launch (two instances per CTA in shared memory, one per CTA and
  * several CTAs per SM in global memory), instances taken longest first.
  * With more than one launch, each runs on a stream the library owns, forked
- * from `stream` and joined back into it by events (stream capture follows
- * the fork).  Instance b gets the
+ * from `stream` and joined back into it by events.  The call copies its
+ * instance table from pageable host memory, so it cannot be captured into a
+ * CUDA graph.  Instance b gets the
  * outputs cs_omp gives for (plans[b], y_dev[b], K[b]):
  *   plans      host array [count] of plans on the current device (a plan may
  *              appear more than once); N <= 2^16; plans with N > 8192 need
