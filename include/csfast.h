@@ -194,10 +194,11 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
  * CUDA graph.  Instance b gets the
  * outputs cs_omp gives for (plans[b], y_dev[b], K[b]):
  *   plans      host array [count] of plans on the current device (a plan may
- *              appear more than once); N <= 2^16; plans with N > 8192 need
- *              the full storage of c (no CS_PLAN_C_* flag)
+ *              appear more than once); plans with 8192 < N <= 2^16 need the
+ *              full storage of c (no CS_PLAN_C_* flag)
  *   y_dev      host array [count] of device pointers, F[M_b] each
- *   K          host array [count], 0 <= K[b] <= min(M_b, 1024)
+ *   K          host array [count], 0 <= K[b] <= M_b, and K[b] <= 1024 for
+ *              N <= 2^16, K[b] <= 4096 for larger N
  *   x_dev      NULL, or host array [count] of device pointers, FP64 [K[b]]
  *   supp_dev   host array [count] of device pointers, int32 [K[b]] (an
  *              entry may be NULL where K[b] = 0)
@@ -206,10 +207,13 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
  * halt as in cs_omp; with t_switch < 0 an instance takes its plan's switch
  * point (N <= 8192) or 32 (larger N: their kernel sums stream c through L2).
  * Instances with N <= 8192 give bit for bit the results of cs_omp on their
- * plan.  Larger ones run the one-CTA radix-16 chains on vectors in global
- * memory, two passes per round trip through a shared-memory tile, where
- * cs_omp runs four-step transforms over the GPU, and agree with it to
- * rounding.  The workspace is allocated stream-ordered on `stream` and freed
+ * plan.  Those with 8192 < N <= 2^16 run the one-CTA radix-16 chains on
+ * vectors in global memory, two passes per round trip through a
+ * shared-memory tile, where cs_omp runs four-step transforms over the GPU,
+ * and agree with it to rounding.  Those with N > 2^16 run cs_omp's
+ * large-plan path (a few whole-GPU launches per iteration), one instance at a
+ * time on a library stream beside the persistent launches, bit for bit as
+ * cs_omp on their plan.  The workspace is allocated stream-ordered on `stream` and freed
  * after the launches.  The call may wait for `stream` while it copies the
  * instance table.  A device-detected error goes to plans[0]'s status word
  * (cs_plan_status).  Errors: CS_ERR_INVALID for bad arguments,

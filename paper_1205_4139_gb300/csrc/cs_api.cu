@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdint>
 #include <map>
 #include <mutex>
 #include <new>
@@ -82,7 +83,7 @@ cudaError_t raise_smem_limit(const void* func, size_t bytes) {
   return e;
 }
 
-// Streams the library forks work onto (k < 8 per device), created on first
+// Streams the library forks work onto (a few per device), created on first
 // use and kept until the process exits.
 cudaError_t fork_stream(int dev, int k, cudaStream_t* out) {
   static std::mutex mu;
@@ -522,8 +523,17 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
   int dev = 0;
   cudaGetDevice(&dev);
   // one launch per element type (kind, precision) and residence (instances
-  // held in shared memory, N <= 8192, or in global memory)
+  // held in shared memory, N <= 8192, or in global memory, N <= 2^16); larger
+  // N: the large-plan path of cs_omp, one instance at a time
   std::vector<MultiItem> group[8];
+  struct Solo {
+    cs_plan_s* p;
+    const void* y;
+    void* x;
+    int* supp;
+    int K, t_switch, idx;
+  };
+  std::vector<Solo> solo;
   for (int64_t b = 0; b < count; ++b) {
     const cs_plan_s* p = plans[b];
     if (!p) return CS_ERR_INVALID;
@@ -535,12 +545,21 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
     if (k < 0 || k > p->v.M) return CS_ERR_INVALID;
     if (p->v.M > 0 && !y_dev[b]) return CS_ERR_INVALID;
     if (k > 0 && (!supp_dev[b] || (x_dev && !x_dev[b]))) return CS_ERR_INVALID;
-    if (p->v.logN > kMaxLogNMulti || k > kMaxK) {
-      set_last_error("cs_omp_batched: N above 2^16 or K above 1024");
+    if (p->v.logN > kMaxLogNMulti) {
+      if (k > kMaxKLarge) {
+        set_last_error("cs_omp_batched: K above 4096 (N > 2^16)");
+        return CS_ERR_UNSUPPORTED;
+      }
+      solo.push_back({plans[b], y_dev[b], x_dev ? x_dev[b] : nullptr, supp_dev[b], k,
+                      h.t_switch >= 0 ? h.t_switch : plan_switch(p), (int)b});
+      continue;
+    }
+    if (k > kMaxK) {
+      set_last_error("cs_omp_batched: K above 1024 (N <= 2^16)");
       return CS_ERR_UNSUPPORTED;
     }
     if (p->v.large && p->v.cfmt != CFMT_FULL) {
-      set_last_error("cs_omp_batched: plans with N > 8192 need the full storage of c");
+      set_last_error("cs_omp_batched: plans with 8192 < N <= 2^16 need the full storage of c");
       return CS_ERR_UNSUPPORTED;
     }
     MultiItem it;
@@ -564,9 +583,12 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
     }
   }
   cudaStream_t st = (cudaStream_t)stream;
-  // launches with the most work first; with several, each runs on a stream of
-  // its own forked from and joined back into `stream`, so that the CTAs of a
-  // later launch fill the SMs an earlier one leaves idle in its tail
+  // Jobs: the persistent launches, most work first, on streams 0..7, and the
+  // large-plan instances on streams 8..11 chosen by plan (instances of one
+  // plan share its workspace, so they stay in order on one stream).  With
+  // more than one job, each stream is forked from `stream` and joined back
+  // into it, so that the CTAs of later launches fill the SMs an earlier one
+  // leaves idle in its tail.
   std::vector<int> order;
   std::vector<double> work(8, 0.0);
   for (int gi = 0; gi < 8; ++gi) {
@@ -574,32 +596,67 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
     if (!group[gi].empty()) order.push_back(gi);
   }
   std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return work[u] > work[v]; });
-  if (order.size() == 1) {
-    std::vector<MultiItem>& g = group[order[0]];
-    CS_CUDA(launch_omp_multi(g.data(), (int64_t)g.size(), h.rel_tol, h.path, iters_dev, resnorm_dev,
-                             plans[0]->v.status, st),
-            "omp_batched kernel");
-    return CS_OK;
-  }
+  struct Job {
+    int stream, group, solo;
+  };
+  std::vector<Job> jobs;
+  for (size_t k = 0; k < order.size(); ++k) jobs.push_back({(int)k, order[k], -1});
+  for (size_t i = 0; i < solo.size(); ++i)
+    jobs.push_back({8 + (int)(((uintptr_t)solo[i].p >> 4) % 4), -1, (int)i});
+  auto run = [&](const Job& j, cudaStream_t s) -> cs_status {
+    if (j.group >= 0) {
+      std::vector<MultiItem>& g = group[j.group];
+      const cudaError_t e = launch_omp_multi(g.data(), (int64_t)g.size(), h.rel_tol, h.path, iters_dev,
+                                             resnorm_dev, plans[0]->v.status, s);
+      return e == cudaSuccess ? CS_OK : cuda_fail(e, "omp_batched kernel");
+    }
+    const Solo& so = solo[(size_t)j.solo];
+    const cs_status r = ensure_ws(so.p, large_omp_ws(so.p->v, so.K, h.path, 1), s);
+    if (r != CS_OK) return r;
+    OmpLaunch a;
+    a.y = so.y;
+    a.batch = 1;
+    a.K = so.K;
+    a.rel_tol = h.rel_tol;
+    a.path = h.path;
+    a.t_switch = so.t_switch;
+    a.x_out = so.x;
+    a.supp_out = so.supp;
+    a.iters_out = iters_dev ? iters_dev + so.idx : nullptr;
+    a.res_out = resnorm_dev ? resnorm_dev + so.idx : nullptr;
+    const cudaError_t e = large_omp(so.p->v, a, so.p->ws, s);
+    return e == cudaSuccess ? CS_OK : cuda_fail(e, "omp_batched large-plan kernels");
+  };
+  if (jobs.size() == 1) return run(jobs[0], st);
   cudaEvent_t fork = nullptr;
   CS_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "omp_batched event");
+  cs_status r = CS_OK;
   cudaError_t e = cudaEventRecord(fork, st);
-  for (size_t k = 0; k < order.size() && e == cudaSuccess; ++k) {
-    std::vector<MultiItem>& g = group[order[k]];
-    cudaStream_t aux = nullptr;
+  std::map<int, cudaStream_t> aux;
+  for (const Job& j : jobs) {
+    if (e != cudaSuccess || aux.count(j.stream)) continue;
+    cudaStream_t s = nullptr;
+    e = fork_stream(dev, j.stream, &s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork, 0);
+    if (e == cudaSuccess) aux[j.stream] = s;
+  }
+  for (const Job& j : jobs) {
+    if (e != cudaSuccess || r != CS_OK) break;
+    r = run(j, aux[j.stream]);
+  }
+  // join every forked stream back, also after a failure: nothing queued on
+  // it may outlive the caller's stream
+  for (const auto& kv : aux) {
     cudaEvent_t done = nullptr;
-    e = fork_stream(dev, (int)k, &aux);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, fork, 0);
-    if (e == cudaSuccess)
-      e = launch_omp_multi(g.data(), (int64_t)g.size(), h.rel_tol, h.path, iters_dev, resnorm_dev,
-                           plans[0]->v.status, aux);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(done, aux);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, done, 0);
+    cudaError_t e2 = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    if (e2 == cudaSuccess) e2 = cudaEventRecord(done, kv.second);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, done, 0);
     if (done) cudaEventDestroy(done);
+    if (e == cudaSuccess) e = e2;
   }
   cudaEventDestroy(fork);
-  CS_CUDA(e, "omp_batched kernels");
+  if (r != CS_OK) return r;
+  CS_CUDA(e, "omp_batched streams");
   return CS_OK;
 }
 

@@ -80,7 +80,7 @@ struct PursuitLaunch {
 // different needs (the request runtime's workers) never lower it under one
 // another between setting it and launching.
 cudaError_t raise_smem_limit(const void* func, size_t bytes);
-// Streams the library forks work onto (k < 8 per device), created on first use.
+// Streams the library forks work onto (a few per device), created on first use.
 cudaError_t fork_stream(int dev, int k, cudaStream_t* out);
 
 // plan construction

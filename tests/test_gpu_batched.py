@@ -9,6 +9,7 @@ kind, precision) and their own K, one persistent kernel per element type.
   exact up to the first oracle top-two gap <= 1e-3, x within 1e-10 / 1e-4
   relative in noiseless cases, ||r|| / ||y||), and agreement with cs_omp's
   four-step path.
+* N > 2^16: cs_omp's large-plan path, bit for bit.
 * the three correlation paths agree; edge cases (K = 0, y = 0, a plan shared
   by several instances, K = M, K = 1024, N = 2^16); refusals.
 """
@@ -199,13 +200,35 @@ def test_largest_sizes_by_properties():
     assert plan.device_error() == 0
 
 
+def test_large_plans_ride_along():
+    """Instances with N > 2^16 (the large-plan path, on library streams)
+    beside one-CTA and global-memory ones: each equals cs_omp on its plan bit
+    for bit, also when its plan is used twice in the call."""
+    specs = [("dft", "fp32", 1 << 17, 8192, 40, None), ("wht", "fp64", 1 << 18, 9000, 24, 40),
+             ("dft", "fp32", 2048, 512, 20, None), ("wht", "fp32", 1 << 15, 4096, 30, None)]
+    plans, ys, Ks, insts = build(specs, 12)
+    plans.append(plans[0])
+    ys.append(ys[0] * 0.5)
+    Ks.append(17)
+    bt = binding.omp_batched(plans, ys, Ks)
+    torch.cuda.synchronize()
+    for b in (0, 1, 2, 4):
+        x, s, it, rn = plans[b].omp(ys[b][None], Ks[b])
+        torch.cuda.synchronize()
+        assert torch.equal(bt.supp[b], s[0]) and torch.equal(bt.x[b], x[0]), b
+        assert int(bt.iters[b]) == int(it[0]) and float(bt.resnorm[b]) == float(rn[0])
+    check_against_oracle(insts[3], bt.x[3].cpu().numpy(), bt.supp[3].cpu().numpy(), int(bt.iters[3]),
+                         float(bt.resnorm[3]), True)
+    assert all(p.device_error() == 0 for p in plans[:4])
+
+
 def test_refusals():
     rng = np.random.default_rng(1)
-    om = synth.draw_omega(1 << 17, 64, rng)
+    om = synth.draw_omega(1 << 17, 5000, rng)
     big = binding.Plan(1 << 17, om, "dft", "fp32")
-    y = torch.zeros(64, dtype=torch.complex64, device="cuda")
-    with pytest.raises(binding.CsError):  # N above 2^16
-        binding.omp_batched([big], [y], [4])
+    y = torch.zeros(5000, dtype=torch.complex64, device="cuda")
+    with pytest.raises(binding.CsError):  # K above 4096 for N > 2^16
+        binding.omp_batched([big], [y], [4097])
     om2 = synth.draw_omega(1 << 14, 2048, rng)
     half = binding.Plan(1 << 14, om2, "dft", "fp32", c_storage="half")
     y2 = torch.zeros(2048, dtype=torch.complex64, device="cuda")
