@@ -291,7 +291,7 @@ def uneven(n_inst: int):
             "device_error": plans[0].device_error()}
 
 
-def config5(N=1 << 22, M=1 << 19, K=4096):
+def huge_instance(N=1 << 22, M=1 << 19, K=4096):
     """The one large instance, once: one partial-DFT complex64
     instance, N = 2^22, M = 2^19, K = 4096, 30 dB, OMP (hybrid at the tuned
     switch point of a K = 256 run) with the FP64 least squares on the GPU.
@@ -554,8 +554,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle instances (default one per core)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement")
     ap.add_argument("--uneven-instances", type=int, default=4096, help="instances of the uneven-batch measurement")
-    ap.add_argument("--config5", action="store_true",
-                    help="run only the one large instance N=2^22, M=2^19, K=4096, 30 dB (minutes of FP64 work)")
+    ap.add_argument("--huge", action="store_true",
+                    help="run only the one partial-DFT instance N=2^22, M=2^19, K=4096, 30 dB")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -564,8 +564,8 @@ def main():
     cores = len(os.sched_getaffinity(0))
     n_cpu = args.cpu_sample or cores
 
-    if args.config5:
-        print(json.dumps(config5()))
+    if args.huge:
+        print(json.dumps(huge_instance()))
         return
 
     if args.impl == "reference":
