@@ -94,6 +94,17 @@ template <class E> __host__ __device__ inline int lstride(int len) { return len 
 struct LState {  // per instance, in the workspace
   int p, done, pad0, pad1;
   double ynorm2, rn2;
+  int ncols, pad2;  // distinct support columns of the four-step split registered so far
+};
+
+// Compact input of pass 2 for a sparse vector (the forward transform of
+// zf(x_Lambda)): Tc[b][k1][c] is pass 1's output at row k1 and the c-th
+// distinct column cols[b][c] of the support; every other column is zero.
+template <class E>
+struct LSparse {
+  const E* Tc;      // NULL: pass 2 reads the dense pass-1 output
+  const int* cols;  // [batch][kc]
+  int kc;
 };
 
 enum { LD_DENSE = 0, LD_ZF = 1, LD_ONES = 2 };
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
                                                    const E* __restrict__ y, const uint32_t* __restrict__ bits,
                                                    typename NormT<E>::V* __restrict__ part_v,
                                                    int* __restrict__ part_j, int nparts,
-                                                   const LState* __restrict__ st) {
+                                                   const LState* __restrict__ st, LSparse<E> sp) {
   using V = typename NormT<E>::V;
   constexpr int C = tile_c<E>(), LC = log_tile_c<E>();
   extern __shared__ __align__(16) unsigned char sm[];
@@ -296,10 +307,23 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
   V* rv = (V*)(sm + L.rv);
   int* rj = (int*)(sm + L.rj);
   const int r0 = blockIdx.x * C;
-  const E* src = T + b * (int64_t)P.N;
   const int tot = C * N2;  // a multiple of kLT
-  for (int q = threadIdx.x; q < tot; q += kLT)
-    cp_async_elem(buf + (q >> n2) * cs + swz<E>(q & (N2 - 1)), src + ((r0 + (q >> n2)) << n2) + (q & (N2 - 1)));
+  if (sp.Tc) {
+    // sparse input: zero rows, then the registered columns of rows r0 ..
+    for (int q = threadIdx.x; q < tot; q += kLT) buf[(q >> n2) * cs + swz<E>(q & (N2 - 1))] = zero<E>();
+    __syncthreads();
+    const int nc = st[b].ncols;
+    const E* tcb = sp.Tc + b * ((int64_t)1 << n1) * sp.kc;
+    const int* cb = sp.cols + b * sp.kc;
+    for (int i = threadIdx.x; i < C * nc; i += kLT) {
+      const int r = i / nc, c = i - r * nc;
+      buf[r * cs + swz<E>(cb[c])] = tcb[(int64_t)(r0 + r) * sp.kc + c];
+    }
+  } else {
+    const E* src = T + b * (int64_t)P.N;
+    for (int q = threadIdx.x; q < tot; q += kLT)
+      cp_async_elem(buf + (q >> n2) * cs + swz<E>(q & (N2 - 1)), src + ((r0 + (q >> n2)) << n2) + (q & (N2 - 1)));
+  }
   if constexpr (DFT) build_position_table(tab, n2);
   cp_async_wait_all();
   __syncthreads();
@@ -364,6 +388,42 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
   if constexpr (SK == SK_H || SK == SK_ARG) {
     if (part_v) block_partial(bv, bj, rv, rj, part_v + b * nparts + blockIdx.x, part_j + b * nparts + blockIdx.x);
   }
+}
+
+// ------------------------------------------------- sparse pass 1
+// Pass 1 of the forward transform of zf(x_Lambda) straight from the support:
+// column i2 of the N1 x N2 view holds the support entries lambda = i2 + N2 i1
+// and pass 1's output there is sum over them of x_lambda w_N^(lambda k1)
+// (DFT: w_N1^(i1 k1) w_N^(i2 k1) = w_N^(lambda k1)) or of
+// x_lambda (-1)^popcount(i1 & k1) (WHT: H_N1 on the columns).  One thread per
+// (k1, registered column c); the entries of a column are summed in the order
+// they joined the support.  Output Tc[b][k1][c] (row stride kc).
+template <class E, bool DFT>
+__global__ void __launch_bounds__(kLT) lsp1_kernel(LDev<E> P, const E* __restrict__ xw, const int* __restrict__ lam,
+                                                   const int* __restrict__ chead, const int* __restrict__ cnext,
+                                                   int K, int kc, int kcl, E* __restrict__ Tc,
+                                                   const LState* __restrict__ st) {
+  const int64_t b = blockIdx.y;
+  if (st[b].done) return;
+  const int nc = st[b].ncols;
+  const int N1 = 1 << P.n1;
+  const int idx = blockIdx.x * kLT + threadIdx.x;
+  if (idx >= N1 * kcl) return;
+  const int k1 = idx / kcl, c = idx - k1 * kcl;
+  if (c >= nc) return;
+  const int* nx = cnext + b * K;
+  const int* lm = lam + b * K;
+  const E* xv = xw + b * K;
+  E acc = zero<E>();
+  for (int k = chead[b * kc + c]; k >= 0; k = nx[k]) {
+    const int l = lm[k];
+    if constexpr (DFT) {
+      acc = add(acc, mul(xv[k], root(P, (int)(((unsigned)l * (unsigned)k1) & (unsigned)(P.N - 1)))));
+    } else {
+      acc = (__popc((l >> P.n2) & k1) & 1) ? sub(acc, xv[k]) : add(acc, xv[k]);
+    }
+  }
+  Tc[b * (int64_t)N1 * kc + (int64_t)k1 * kc + c] = acc;
 }
 
 // ------------------------------------------------------ fast correlation
@@ -527,6 +587,16 @@ struct LOmpArgs {
   int nyp;
   double* terms;   // [batch][gmax][3] per-CTA shares of ||u||^2 and u^H z
   int gmax;
+  // support columns of the four-step split (NULL: not kept), for the sparse
+  // pass 1: colmap[b][i2] = registered index or -1; cols / chead / ctail per
+  // registered column (at most kc); cnext[b][k] the next support index in k's
+  // column or -1
+  int* colmap;
+  int* cols;
+  int* chead;
+  int* ctail;
+  int* cnext;
+  int kc;
 };
 
 // Boundaries of G blocks of equal area over p rows of a lower triangle
@@ -776,6 +846,22 @@ __device__ void ls_w_phase(const LOmpArgs<E>& a, int G, int gi, int64_t b) {
     if (xz) xz[l] = e;
     a.lam[b * K + p] = l;
     a.bits[b * (int64_t)(N >> 5) + (l >> 5)] |= 1u << (l & 31);
+    if (a.colmap) {  // register l's column (append order within a column)
+      const int n2 = a.P.n2, i2 = l & ((1 << n2) - 1);
+      int* cm = a.colmap + (b << n2);
+      int c = cm[i2];
+      if (c < 0 && S->ncols < a.kc) {
+        c = S->ncols;
+        S->ncols = c + 1;
+        cm[i2] = c;
+        a.cols[b * a.kc + c] = i2;
+        a.chead[b * a.kc + c] = p;
+      } else if (c >= 0) {
+        a.cnext[b * K + a.ctail[b * a.kc + c]] = p;
+      }
+      if (c >= 0) a.ctail[b * a.kc + c] = p;
+      a.cnext[b * K + p] = -1;
+    }
   }
   // the last CTA of this instance to get here applies step 8
   __syncthreads();
@@ -848,13 +934,13 @@ cudaError_t run_col(const LDev<E>& P, const E* in, int64_t in_stride, E* out, co
 template <class E, bool DFT, int SK>
 cudaError_t run_row(const LDev<E>& P, const E* T, int neg, double scl, E* out, const E* y, const uint32_t* bits,
                     typename NormT<E>::V* pv, int* pj, int nparts, const LState* st, int64_t batch,
-                    cudaStream_t s) {
+                    cudaStream_t s, LSparse<E> sp = LSparse<E>{nullptr, nullptr, 0}) {
   const size_t smem = pass_layout<E>(1 << P.n2).total;
   cudaError_t e = allow_smem(lrow_kernel<E, DFT, SK>, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((1u << P.n1) / tile_c<E>(), (unsigned)batch);
   lrow_kernel<E, DFT, SK><<<grid, kLT, smem, s>>>(P, T, neg, (typename FT<E>::R)scl, out, y, bits, pv, pj,
-                                                  nparts, st);
+                                                  nparts, st, sp);
   return cudaGetLastError();
 }
 
@@ -987,8 +1073,8 @@ cudaError_t fast_t(const PlanView& Pv, const void* h0, const int32_t* supp, cons
 // ------------------------------------------------------------------- OMP
 template <class E>
 struct LOmpWs {
-  size_t st, h0, T, Z, xz, bits, B, z, x, u, xw, lam, pv, pj, yp, tm, total;
-  int nparts, nyp, gmax;
+  size_t st, h0, T, Z, xz, bits, B, z, x, u, xw, lam, pv, pj, yp, tm, cm, cl, ch, ct, cn, Tc, total;
+  int nparts, nyp, gmax, kc;
 };
 
 template <class E>
@@ -1029,6 +1115,16 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
     L.gmax = (int)(g < 1 ? 1 : (g > 256 ? 256 : g));
   }
   L.tm = o;   o = al16(o + (size_t)batch * L.gmax * 3 * sizeof(double));
+  // the sparse pass 1 of the transform path: registered support columns, at
+  // most kc = min(K, N2 / 2) (beyond that the dense pass 1 is as cheap)
+  L.kc = conv ? (K < (1 << (P.n2 - 1)) ? K : (1 << (P.n2 - 1))) : 0;
+  const size_t kcs = (size_t)L.kc;
+  L.cm = o;   o = al16(o + (kcs ? (size_t)batch * ((size_t)1 << P.n2) * sizeof(int) : 0));
+  L.cl = o;   o = al16(o + (size_t)batch * kcs * sizeof(int));
+  L.ch = o;   o = al16(o + (size_t)batch * kcs * sizeof(int));
+  L.ct = o;   o = al16(o + (size_t)batch * kcs * sizeof(int));
+  L.cn = o;   o = al16(o + (kcs ? (size_t)batch * Kc * sizeof(int) : 0));
+  L.Tc = o;   o = al16(o + (size_t)batch * ((size_t)1 << P.n1) * kcs * sizeof(E));
   L.total = o;
   return L;
 }
@@ -1070,9 +1166,19 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
   A.nyp = L.nyp;
   A.terms = (double*)(w + L.tm);
   A.gmax = L.gmax;
+  A.kc = L.kc;
+  A.colmap = L.kc ? (int*)(w + L.cm) : nullptr;
+  A.cols = (int*)(w + L.cl);
+  A.chead = (int*)(w + L.ch);
+  A.ctail = (int*)(w + L.ct);
+  A.cnext = (int*)(w + L.cn);
+  E* Tc = (E*)(w + L.Tc);
   const size_t Nv = (size_t)batch * P.N * sizeof(E);
   cudaError_t e;
   if ((e = cudaMemsetAsync(A.st, 0, (size_t)batch * sizeof(LState), s)) != cudaSuccess) return e;
+  if (A.colmap &&
+      (e = cudaMemsetAsync(A.colmap, 0xff, (size_t)batch * ((size_t)1 << P.n2) * sizeof(int), s)) != cudaSuccess)
+    return e;
   if ((e = cudaMemsetAsync(A.bits, 0, (size_t)batch * (P.N >> 5) * sizeof(uint32_t), s)) != cudaSuccess) return e;
   if (Z && (e = cudaMemsetAsync(Z, 0, Nv, s)) != cudaSuccess) return e;
   if (A.xz && (e = cudaMemsetAsync(A.xz, 0, Nv, s)) != cudaSuccess) return e;
@@ -1097,10 +1203,21 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
                                 A.st, batch, s, &np)) != cudaSuccess)
         return e;
     } else {  // r = y - Phi x by a forward transform of zf(x), then h = A^H zf(r)
-      if ((e = run_col<E, DFT, LD_DENSE>(P, A.xz, P.N, T, A.st, batch, s)) != cudaSuccess) return e;
-      if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s)) !=
-          cudaSuccess)
-        return e;
+      const int sup = t - 1;
+      if (sup <= L.kc) {  // pass 1 from the support's columns, pass 2 from the compact result
+        const int N1 = 1 << P.n1;
+        const dim3 g1((unsigned)(((int64_t)N1 * sup + kLT - 1) / kLT), (unsigned)batch);
+        lsp1_kernel<E, DFT><<<g1, kLT, 0, s>>>(P, A.xw, A.lam, A.chead, A.cnext, a.K, L.kc, sup, Tc, A.st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = run_row<E, DFT, SK_RES>(P, nullptr, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s,
+                                         LSparse<E>{Tc, A.cols, L.kc})) != cudaSuccess)
+          return e;
+      } else {
+        if ((e = run_col<E, DFT, LD_DENSE>(P, A.xz, P.N, T, A.st, batch, s)) != cudaSuccess) return e;
+        if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s)) !=
+            cudaSuccess)
+          return e;
+      }
       if ((e = run_col<E, DFT, LD_DENSE>(P, Z, P.N, T, A.st, batch, s)) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_ARG>(P, T, DFT, isq, nullptr, nullptr, A.bits, A.part_v, A.part_j, L.nparts,
                                        A.st, batch, s)) != cudaSuccess)
