@@ -111,12 +111,13 @@ void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg)
 // paper_1205_4139_gb300.switch_curves: OMP per-iteration cost of kernel sums
 // and of transforms versus t, M = N/4, partial DFT and WHT): the t above
 // which transforms are cheaper per iteration, by log2 N.  One-CTA plans
-// (batches of instances in shared memory) cross near 64; large plans (one
-// instance spread over the GPU, least squares and launch latency shared by
-// both paths) between about 70 and 200.
+// (batches of instances in shared memory) cross near 64.  Large plans (one
+// instance spread over the GPU) cross late for N <= 2^18, where the least
+// squares and the launches shared by both paths dominate an iteration and
+// the kernel sums over N entries are cheap, and near 100 from N = 2^20 on.
 static int gb300_switch(int logN) {
   if (logN <= kMaxLogN) return 64;
-  static const int table[] = {160, 112, 96, 80, 80, 80, 96, 112, 112, 112, 112};  // log2 N = 14 .. 24
+  static const int table[] = {512, 400, 384, 384, 320, 200, 96, 96, 96, 96, 96};  // log2 N = 14 .. 24
   const int i = logN - 14;
   return table[i < 0 ? 0 : (i > 10 ? 10 : i)];
 }
