@@ -571,7 +571,7 @@ struct LOmpArgs {
   int* iters_out;
   double* res_out;
   E* h0;           // [batch][N]
-  E* xz;           // [batch][N] zero-filled x in the working precision (NULL: kernel sums only)
+  E* xz;           // [batch][N] zero-filled x in the working precision, or NULL (not kept)
   uint32_t* bits;  // [batch][N / 32] support bitmap
   W* B;            // [batch][K(K+1)/2]
   W* z;            // [batch][K]
@@ -1093,7 +1093,7 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
   L.h0 = o;   o = al16(o + Nv);
   L.T = o;    o = al16(o + Nv);
   L.Z = o;    o = al16(o + (conv ? Nv : 0));
-  L.xz = o;   o = al16(o + (conv ? Nv : 0));
+  L.xz = o;
   L.bits = o; o = al16(o + (size_t)batch * (P.N >> 5) * sizeof(uint32_t));
   L.B = o;    o = al16(o + (size_t)batch * ((Kc * (Kc + 1)) / 2) * sizeof(W));
   L.z = o;    o = al16(o + (size_t)batch * Kc * sizeof(W));
@@ -1115,9 +1115,9 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
     L.gmax = (int)(g < 1 ? 1 : (g > 256 ? 256 : g));
   }
   L.tm = o;   o = al16(o + (size_t)batch * L.gmax * 3 * sizeof(double));
-  // the sparse pass 1 of the transform path: registered support columns, at
-  // most kc = min(K, N2 / 2) (beyond that the dense pass 1 is as cheap)
-  L.kc = conv ? (K < (1 << (P.n2 - 1)) ? K : (1 << (P.n2 - 1))) : 0;
+  // the sparse pass 1 of the transform path: registered support columns,
+  // kc = min(K, N2) of them (a support never spans more than N2 columns)
+  L.kc = conv ? (K < (1 << P.n2) ? K : (1 << P.n2)) : 0;
   const size_t kcs = (size_t)L.kc;
   L.cm = o;   o = al16(o + (kcs ? (size_t)batch * ((size_t)1 << P.n2) * sizeof(int) : 0));
   L.cl = o;   o = al16(o + (size_t)batch * kcs * sizeof(int));
@@ -1151,7 +1151,7 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
   A.h0 = (E*)(w + L.h0);
   E* T = (E*)(w + L.T);
   E* Z = a.path != 0 ? (E*)(w + L.Z) : nullptr;
-  A.xz = a.path != 0 ? (E*)(w + L.xz) : nullptr;
+  A.xz = nullptr;  // the transform path builds pass 1 from the support's columns
   A.bits = (uint32_t*)(w + L.bits);
   A.B = (W*)(w + L.B);
   A.z = (W*)(w + L.z);
@@ -1181,7 +1181,6 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
     return e;
   if ((e = cudaMemsetAsync(A.bits, 0, (size_t)batch * (P.N >> 5) * sizeof(uint32_t), s)) != cudaSuccess) return e;
   if (Z && (e = cudaMemsetAsync(Z, 0, Nv, s)) != cudaSuccess) return e;
-  if (A.xz && (e = cudaMemsetAsync(A.xz, 0, Nv, s)) != cudaSuccess) return e;
   const size_t ls_smem = (size_t)(a.K > 0 ? a.K : 1) * sizeof(W);
   if ((e = allow_smem(lls_one_kernel<E>, ls_smem)) != cudaSuccess) return e;
   if ((e = allow_smem(lls_u_kernel<E>, ls_smem)) != cudaSuccess) return e;
@@ -1202,22 +1201,15 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
       if ((e = run_fast<E, DFT>(P, A.h0, A.lam, A.xw, t - 1, a.K, A.bits, nullptr, A.part_v, A.part_j, L.nparts,
                                 A.st, batch, s, &np)) != cudaSuccess)
         return e;
-    } else {  // r = y - Phi x by a forward transform of zf(x), then h = A^H zf(r)
-      const int sup = t - 1;
-      if (sup <= L.kc) {  // pass 1 from the support's columns, pass 2 from the compact result
-        const int N1 = 1 << P.n1;
-        const dim3 g1((unsigned)(((int64_t)N1 * sup + kLT - 1) / kLT), (unsigned)batch);
-        lsp1_kernel<E, DFT><<<g1, kLT, 0, s>>>(P, A.xw, A.lam, A.chead, A.cnext, a.K, L.kc, sup, Tc, A.st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = run_row<E, DFT, SK_RES>(P, nullptr, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s,
-                                         LSparse<E>{Tc, A.cols, L.kc})) != cudaSuccess)
-          return e;
-      } else {
-        if ((e = run_col<E, DFT, LD_DENSE>(P, A.xz, P.N, T, A.st, batch, s)) != cudaSuccess) return e;
-        if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s)) !=
-            cudaSuccess)
-          return e;
-      }
+    } else {  // r = y - Phi x by a forward transform of zf(x), then h = A^H zf(r):
+              // pass 1 from the support's columns, pass 2 from the compact result
+      const int N1 = 1 << P.n1, kcl = (t - 1) < L.kc ? (t - 1) : L.kc;
+      const dim3 g1((unsigned)(((int64_t)N1 * kcl + kLT - 1) / kLT), (unsigned)batch);
+      lsp1_kernel<E, DFT><<<g1, kLT, 0, s>>>(P, A.xw, A.lam, A.chead, A.cnext, a.K, L.kc, kcl, Tc, A.st);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = run_row<E, DFT, SK_RES>(P, nullptr, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s,
+                                       LSparse<E>{Tc, A.cols, L.kc})) != cudaSuccess)
+        return e;
       if ((e = run_col<E, DFT, LD_DENSE>(P, Z, P.N, T, A.st, batch, s)) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_ARG>(P, T, DFT, isq, nullptr, nullptr, A.bits, A.part_v, A.part_j, L.nparts,
                                        A.st, batch, s)) != cudaSuccess)
