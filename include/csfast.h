@@ -114,9 +114,10 @@ enum { CS_PLAN_C_HALF = 1u, CS_PLAN_C_INT = 2u };
 cs_status cs_plan_create_ex(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
                             uint32_t flags, void* stream, cs_plan_t* out);
 
-/* Device bytes held by the plan's tables (slot maps, c in its storage format,
- * twiddles, status word), not counting the workspace or the chain twiddles
- * shared by all plans of one N. */
+/* Device bytes held by the plan's tables (slot maps, Omega grouped by
+ * transform row for N > 8192, c in its storage format, twiddles, status
+ * word), not counting the workspace or the chain twiddles shared by all
+ * plans of one N. */
 cs_status cs_plan_memory(cs_plan_t plan, int64_t* table_bytes);
 
 /* Release the plan's device memory (synchronises the device first). */

@@ -25,6 +25,8 @@ struct cs_plan_s {
   int t_switch_tuned = -1;  // set by cs_plan_tune
   int* d_slot = nullptr;
   int* d_slot_chain = nullptr;  // 8192 < N <= 2^16, DFT: slot map in the one-CTA chains' order
+  int* d_om_off = nullptr;      // large plans: Omega by pass-2 row (offsets)
+  int2* d_om_ent = nullptr;     //   and entries (j, m)
   void* d_tw64 = nullptr;
   void* d_tw32 = nullptr;
   void* d_c64 = nullptr;
@@ -130,8 +132,8 @@ static int plan_switch(const cs_plan_s* p) {
 
 static void plan_free(cs_plan_s* p) {
   if (!p) return;
-  void* bufs[] = {p->d_slot, p->d_slot_chain, p->d_tw64, p->d_tw32, p->d_c64,   p->d_c32,
-                  p->d_ci,   p->d_lt64,       p->d_lt32, p->d_status, p->ws};
+  void* bufs[] = {p->d_slot, p->d_slot_chain, p->d_om_off, p->d_om_ent, p->d_tw64, p->d_tw32,
+                  p->d_c64,  p->d_c32,        p->d_ci,     p->d_lt64,   p->d_lt32, p->d_status, p->ws};
   for (void* b : bufs) {
     if (!b) continue;
     if (p->ordered) cudaFreeAsync(b, p->home);
@@ -235,6 +237,30 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
              "copy slot");
     PLAN_TRY(chain_twiddles(logN, st, &p->v.ctw64, &p->v.ctw32), "chain twiddles");
   }
+  // large plans: Omega grouped by the pass-2 row it comes out of (counting
+  // sort), so that the residual sink visits only Omega's positions
+  std::vector<int32_t> om_off;
+  std::vector<int2> om_ent;
+  if (large && M > 0) {
+    const int n1 = p->v.n1, n2 = p->v.n2, N1 = 1 << n1;
+    auto row_of = [&](int j) { return kind == CS_DFT ? (j & (N1 - 1)) : (j >> n2); };
+    om_off.assign((size_t)N1 + 1, 0);
+    for (int64_t m = 0; m < M; ++m) ++om_off[(size_t)row_of(omega_host[m]) + 1];
+    for (int r = 0; r < N1; ++r) om_off[(size_t)r + 1] += om_off[(size_t)r];
+    om_ent.resize((size_t)M);
+    std::vector<int32_t> fill(om_off.begin(), om_off.end() - 1);
+    for (int64_t m = 0; m < M; ++m) {
+      const int j = omega_host[m];
+      om_ent[(size_t)fill[(size_t)row_of(j)]++] = make_int2(j, (int)m);
+    }
+    PLAN_TRY(plan_alloc(p, (void**)&p->d_om_off, om_off.size() * sizeof(int32_t)), "cudaMalloc Omega rows");
+    PLAN_TRY(cudaMemcpyAsync(p->d_om_off, om_off.data(), om_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             st),
+             "copy Omega rows");
+    PLAN_TRY(plan_alloc(p, (void**)&p->d_om_ent, om_ent.size() * sizeof(int2)), "cudaMalloc Omega rows");
+    PLAN_TRY(cudaMemcpyAsync(p->d_om_ent, om_ent.data(), om_ent.size() * sizeof(int2), cudaMemcpyHostToDevice, st),
+             "copy Omega rows");
+  }
   if (kind == CS_DFT && !large) {
     PLAN_TRY(plan_alloc(p, &p->d_tw64, (size_t)N * sizeof(double2)), "cudaMalloc twiddles");
     if (prec == CS_FP32) PLAN_TRY(plan_alloc(p, &p->d_tw32, (size_t)N * sizeof(float2)), "cudaMalloc twiddles");
@@ -261,6 +287,8 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
   p->v.lt64 = p->d_lt64;
   p->v.lt32 = p->d_lt32;
   p->v.ci = p->d_ci;
+  p->v.om_off = p->d_om_off;
+  p->v.om_ent = p->d_om_ent;
   if (!large) {
     p->v.slot_chain = p->d_slot;
     p->v.ctw64 = p->d_tw64;
@@ -358,6 +386,7 @@ size_t solve_footprint(int64_t N, int64_t M, int32_t kind, int32_t prec, int32_t
          (16 + (v.fp32 ? 8 : 0));
   if (v.large) b += (size_t)N * wb;  // kernel-vector scratch while the plan is built
   if (v.dft && v.large && logN <= kMaxLogNMulti) b += (size_t)N * 4;  // chain-order slot map
+  if (v.large) b += ((size_t)1 << v.n1) * 4 + 4 + (size_t)M * 8;      // Omega grouped by pass-2 row
   size_t ws = 0;
   if (algo == 0) ws = v.large ? large_omp_ws(v, K, CS_PATH_HYBRID, 1) : omp_workspace_bytes(v, K, 1);
   else if (v.large) ws = large_pursuit_ws(v, K, algo == 2 ? 0 : 1, 0, 1);

@@ -44,6 +44,11 @@ struct PlanView {
   const int* slot_chain;
   const void* ctw64;
   const void* ctw32;
+  // large plans: Omega grouped by the row of the four-step view that pass 2
+  // produces it in (DFT: j mod N1, WHT: j / N2): entries om_ent[om_off[r] ..
+  // om_off[r + 1]) = (j, m) with j = Omega_m
+  const int* om_off;
+  const int2* om_ent;
 };
 
 enum { CFMT_FULL = 0, CFMT_HALF = 1, CFMT_INT = 2 };

@@ -49,6 +49,8 @@ struct LDev {
   using W = typename FT<E>::W;
   int N, logN, M, n1, n2, wsh;
   const int* __restrict__ slot;  // [N] natural order: m if j = Omega_m, else -1
+  const int* __restrict__ om_off;   // Omega by pass-2 row: offsets [N1 + 1] (NULL if M = 0)
+  const int2* __restrict__ om_ent;  //   entries (j, m), grouped by row
   const E* __restrict__ tw1;     // DIF twiddles of the N1 chain
   const E* __restrict__ tw2;     // DIF twiddles of the N2 chain
   const E* __restrict__ wlo;     // w_N^m, m < 2^wsh
@@ -69,6 +71,8 @@ LDev<E> ldev(const PlanView& P) {
   d.n2 = P.n2;
   d.wsh = P.wsh;
   d.slot = P.slot;
+  d.om_off = P.om_off;
+  d.om_ent = P.om_ent;
   constexpr bool f32 = sizeof(typename FT<E>::R) == 4;
   const E* t = (const E*)(f32 ? P.lt32 : P.lt64);
   const int N1 = 1 << P.n1, N2 = 1 << P.n2;
@@ -332,6 +336,27 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
   E* dst = out ? out + b * (int64_t)P.N : nullptr;
   const E* yb = y ? y + b * (int64_t)P.M : nullptr;
   const uint32_t* bb = bits ? bits + b * (int64_t)(P.N >> 5) : nullptr;
+  if constexpr (SK == SK_RES) {
+    // only Omega's outputs are wanted: visit the members of Omega in this
+    // CTA's rows (grouped by row in the plan) instead of every output's slot
+    if (!neg && P.om_off) {
+      const int e0 = __ldg(P.om_off + r0), e1 = __ldg(P.om_off + r0 + C);
+      for (int e = e0 + (int)threadIdx.x; e < e1; e += kLT) {
+        const int2 jm = __ldg(P.om_ent + e);  // (j, m)
+        const int j = jm.x;
+        int c, pos;
+        if constexpr (DFT) {  // row k1 = j mod N1, frequency k2 = j / N1 at its chain position
+          c = (j & ((1 << n1) - 1)) - r0;
+          pos = tab[j >> n1];
+        } else {              // row j / N2, natural position j mod N2
+          c = (j >> n2) - r0;
+          pos = j & (N2 - 1);
+        }
+        dst[j] = sub(yb[jm.y], scale(buf[c * cs + swz<E>(pos)], scl));
+      }
+      return;
+    }
+  }
   V bv = (V)-1;
   int bj = 0x7fffffff;
   for (int q0 = threadIdx.x; q0 < tot; q0 += kU * kLT) {
