@@ -113,13 +113,16 @@ void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg)
 // paper_1205_4139_gb300.switch_curves: OMP per-iteration cost of kernel sums
 // and of transforms versus t, M = N/4, partial DFT and WHT): the t above
 // which transforms are cheaper per iteration, by log2 N.  One-CTA plans
-// (batches of instances in shared memory) cross near 64.  Large plans (one
-// instance spread over the GPU) cross late for N <= 2^18, where the least
-// squares and the launches shared by both paths dominate an iteration and
-// the kernel sums over N entries are cheap, and near 100 from N = 2^20 on.
+// (batches of instances in shared memory) cross near 64.  A large plan (one
+// instance spread over the GPU) measured alone crosses late for N <= 2^18,
+// where the least squares and the launches shared by both paths dominate an
+// iteration, and near 100 from N = 2^20 on; the default switches earlier for
+// N <= 2^19 (128 to 160), because several solves at once (the request
+// runtime) share L2, which the kernel sums stream c through, and the
+// transform path's cost does not grow with t.
 static int gb300_switch(int logN) {
   if (logN <= kMaxLogN) return 64;
-  static const int table[] = {512, 400, 384, 384, 320, 200, 96, 96, 96, 96, 96};  // log2 N = 14 .. 24
+  static const int table[] = {160, 128, 128, 128, 128, 128, 96, 96, 96, 96, 96};  // log2 N = 14 .. 24
   const int i = logN - 14;
   return table[i < 0 ? 0 : (i > 10 ? 10 : i)];
 }

@@ -63,5 +63,5 @@ def test_tune_rejects_bad_arguments():
 
 def test_untuned_large_plan_uses_measured_crossover():
     om = synth.draw_omega(1 << 16, 8192, np.random.default_rng(2))
-    assert binding.Plan(1 << 16, om, "dft", "fp32").switch_point() == 384
-    assert binding.Plan(1 << 14, om[om < (1 << 14)], "wht", "fp32").switch_point() == 512
+    assert binding.Plan(1 << 16, om, "dft", "fp32").switch_point() == 128
+    assert binding.Plan(1 << 14, om[om < (1 << 14)], "wht", "fp32").switch_point() == 160
