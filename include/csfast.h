@@ -131,8 +131,8 @@ cs_status cs_plan_info(cs_plan_t plan, int64_t* N, int64_t* M, int32_t* kind, in
                        int32_t* t_switch_default);
 
 /* The switch point calls with t_switch < 0 use: cs_plan_tune's, if it has
- * run on this plan, else the GB300 crossover for the plan's N (64 for
- * N <= 8192; 200 to 512 for 2^14 <= N <= 2^19; 96 for larger N). */
+ * run on this plan, else a GB300 default for the plan's N (64 for N <= 8192;
+ * 128 to 160 for 2^14 <= N <= 2^19; 96 for larger N). */
 cs_status cs_plan_switch(cs_plan_t plan, int32_t* t_switch);
 
 /* Errors the kernels detected on the device since the last call (0 = none;
