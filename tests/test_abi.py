@@ -57,8 +57,25 @@ def test_host_side_validation_without_gpu():
     assert L.cs_omp_batched(None, 2, None, None, None, None, None, None, None, None) == 1   # missing arrays
     bad = binding.Halt(-1.0, 2, -1, 0)
     assert L.cs_omp_batched(None, 0, None, None, ctypes.byref(bad), None, None, None, None, None) == 1
+    one = (ctypes.c_void_p * 1)(None)
+    k1 = (ctypes.c_int32 * 1)(1)
+    assert L.cs_omp_batched(one, 1, one, k1, None, None, one, None, None, None) == 1  # NULL plan
     om4 = (ctypes.c_int32 * 2)(1, 5)
     assert L.cs_plan_create_ex(16, om4, 2, 0, 0, 1, None, ctypes.byref(h)) == 1   # half storage on a WHT plan
     assert L.cs_plan_create_ex(16, om4, 2, 1, 0, 2, None, ctypes.byref(h)) == 1   # integer storage on a DFT plan
     assert L.cs_plan_create_ex(16, om4, 2, 1, 0, 3, None, ctypes.byref(h)) == 1   # both
     assert L.cs_plan_create_ex(16, om4, 2, 1, 0, 8, None, ctypes.byref(h)) == 1   # unknown flag
+
+
+def test_batch_wrapper_checks_arguments_on_the_host():
+    """binding.Batch rejects mismatched lists and inputs that are not device
+    vectors of the plan's length before it reaches the library."""
+    torch = pytest.importorskip("torch")
+
+    class FakePlan:
+        M, kind, dtype = 8, "wht", torch.float64
+
+    with pytest.raises(ValueError):
+        binding.Batch([FakePlan()], [], [1])
+    with pytest.raises(ValueError):  # a host tensor
+        binding.Batch([FakePlan()], [torch.zeros(8, dtype=torch.float64)], [1])
