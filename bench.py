@@ -46,33 +46,117 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 # ------------------------------------------------------------------ oracle leg
+# Instances of the 1024-instance batch the oracle solves: spread over the
+# batch, including instances that land on reused slots of the persistent
+# kernel (high indices).
+SAMPLE = [0, 1, 151, 303, 304, 455, 607, 608, 609, 700, 811, 900, 1000, 1021, 1022, 1023]
+
+
 def _oracle_worker(args):
     os.environ["OMP_NUM_THREADS"] = "1"
-    kind, N, omega, ys, K = args
+    kind, N, omega, ys, K, record = args
     from oracle import matrices, omp as oomp
     Phi = matrices.sensing_rows(kind, N, omega)
     out = []
     for y in ys:
-        r = oomp.omp(Phi, y.astype(np.complex128), K)
-        out.append(len(r["support"]))
+        r = oomp.omp(Phi, y.astype(np.complex128 if kind == "dft" else np.float64), K, record_h=record)
+        if not record:
+            out.append(len(r["support"]))
+            continue
+        out.append({"support": r["support"], "x": np.asarray(r["x"]), "iters": r["iters"], "gap": r["gap"],
+                    "halt": r["halt"], "rn": r["resnorm"][-1] / r["ynorm"] if r["resnorm"] else 0.0,
+                    "h": np.stack(r["h"]) if r["h"] else None})
     return out
 
 
-def oracle_throughput(inst, n_inst: int, cores: int) -> tuple[float, float]:
-    """Time the FP64 oracle (Algorithm 1.1, dense Phi^H r) on n_inst instances
-    spread over `cores` spawned single-threaded processes.  Returns
-    (solves/s, wall seconds)."""
+def _oracle_transform_worker(spec):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from oracle import transform as tro
+    om, yv = synth.uneven_instance(spec)
+    r = tro.omp(spec["kind"], spec["N"], om, yv.astype(np.complex128 if spec["kind"] == "dft" else np.float64),
+                spec["K"])
+    return {"support": r["support"], "x": np.asarray(r["x"]), "iters": r["iters"], "gap": r["gap"],
+            "halt": r["halt"], "rn": r["resnorm"][-1] / r["ynorm"] if r["resnorm"] else 0.0}
+
+
+def oracle_throughput(inst, idx, cores: int, record: bool = False):
+    """Time the FP64 oracle (Algorithm 1.1, dense Phi^H r) on the instances
+    `idx` of the batch, spread over `cores` spawned single-threaded
+    processes.  Returns (solves/s, wall seconds, per-instance results in the
+    order of idx; with `record`, supports, x, ||r||/||y|| and every h)."""
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
-    ys = inst["Y"][:n_inst]
-    chunks = [ys[i::cores] for i in range(cores)]
+    idx = list(idx)
+    ys = inst["Y"][idx]
+    chunks = [list(range(i, len(idx), cores)) for i in range(cores)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
-        pool.map(_oracle_worker, [(inst["kind"], inst["N"], inst["omega"], ys[:0], inst["K"])] * cores)  # warm
+        pool.map(_oracle_worker, [(inst["kind"], inst["N"], inst["omega"], ys[:0], inst["K"], False)] * cores)  # warm
         t0 = time.perf_counter()
-        pool.map(_oracle_worker, [(inst["kind"], inst["N"], inst["omega"], c, inst["K"]) for c in chunks])
+        res = pool.map(_oracle_worker, [(inst["kind"], inst["N"], inst["omega"], ys[c], inst["K"], record)
+                                        for c in chunks])
         dt = time.perf_counter() - t0
-    return n_inst / dt, dt
+    out = [None] * len(idx)
+    for c, r in zip(chunks, res):
+        for i, v in zip(c, r):
+            out[i] = v
+    return len(idx) / dt, dt, out
+
+
+def uneven_sample(n_inst: int, count: int = 16, max_work: float = 2e9) -> list[int]:
+    """Instances of the uneven batch the transform oracle solves: `count`
+    indices spread over the batch among those whose dense least squares
+    (M K^3 / 3 flops over a run) stays below max_work, so the oracle leg ends
+    in seconds."""
+    specs = synth.uneven_batch(n_inst, seed=0)
+    ok = [i for i, sp in enumerate(specs) if sp["M"] * sp["K"] ** 3 / 3 <= max_work]
+    step = max(1, len(ok) // count)
+    return ok[::step][:count]
+
+
+def oracle_refs(cores: int, n_uneven: int):
+    """FP64 oracle results the accuracy report compares with, computed before
+    any GPU call: the single WHT FP64 instance, and the sample of the uneven
+    batch (transform oracle)."""
+    c1 = synth.make_batch(**synth.CONFIG_WHT_FP64_SINGLE)
+    ctx = mp.get_context("spawn")
+    idx = uneven_sample(n_uneven)
+    specs = synth.uneven_batch(n_uneven, seed=0)
+    with ctx.Pool(cores) as pool:
+        r1 = pool.apply_async(_oracle_worker, [("wht", c1["N"], c1["omega"], c1["Y"], c1["K"], True)])
+        ru = pool.map(_oracle_transform_worker, [specs[i] for i in idx])
+        r1 = r1.get()[0]
+    return {"config1": r1, "uneven": dict(zip(idx, ru))}
+
+
+def _rel_inf(a, b):
+    d = np.max(np.abs(b))
+    return float(np.max(np.abs(np.asarray(a) - b)) / (d if d > 0 else 1.0))
+
+
+def compare_run(ref, supp, iters, x, rn):
+    """One instance against its oracle run: support equal up to the first
+    near tie (top-two gap <= 1e-3), and where the whole run is comparable the
+    iteration count, the l_inf relative x error and the ||r||/||y|| error."""
+    near = next((t for t, g in enumerate(ref["gap"]) if g <= 1e-3), len(ref["gap"]))
+    got = [int(v) for v in supp[: int(iters)]]
+    out = {"support_prefix_equal": got[:near] == list(ref["support"][:near]), "whole_run": near == len(ref["gap"])}
+    if out["whole_run"]:
+        out["iters_equal"] = int(iters) == int(ref["iters"])
+        xr = np.asarray(ref["x"])
+        n = min(int(iters), len(xr))
+        out["x_err"] = _rel_inf(np.asarray(x)[:n], xr[:n]) if n else 0.0
+        out["rn_err"] = abs(float(rn) - float(ref["rn"]))
+    return out
+
+
+def summarize(rows):
+    """Worst errors over the compared instances."""
+    whole = [r for r in rows if r["whole_run"]]
+    return {"instances": len(rows), "support_prefix_equal": sum(r["support_prefix_equal"] for r in rows),
+            "whole_runs_compared": len(whole), "iters_equal": sum(r["iters_equal"] for r in whole),
+            "x_err_max": max((r["x_err"] for r in whole), default=None),
+            "rn_abs_err_max": max((r["rn_err"] for r in whole), default=None)}
 
 
 # ---------------------------------------------------------------- clock sampler
@@ -171,7 +255,7 @@ def _events_ms(fn, steps, warmup, stream, flush=None):
     return [a.elapsed_time(b) for a, b in out]
 
 
-def secondary(args, dev, plan, inst, stream, flush):
+def secondary(args, dev, plan, inst, stream, flush, refs=None):
     """Measurements beside the headline (not part of the timed step):
     subspace pursuit on the same batch; single-instance latency on the
     partial-WHT FP64 case (N=1024, M=256, K=16, noiseless); fast vs
@@ -225,6 +309,12 @@ def secondary(args, dev, plan, inst, stream, flush):
         assert int(t1.item()) > 0
     out["omp_wht_fp64_single_latency"] = {"config": "partial WHT FP64, N=1024, M=256, K=16, noiseless, 1 instance; "
                                                     "one solve in a CUDA graph, 10^4 replays", **lat}
+    if refs and refs.get("config1"):
+        r1c = refs["config1"]
+        row = compare_run(r1c, s1.cpu().numpy()[0], t1.cpu().numpy()[0], x1.cpu().numpy()[0], r1.cpu().numpy()[0])
+        h1, _ = p1.correlate(y1)
+        out["omp_wht_fp64_single_latency"]["accuracy"] = {
+            **row, "h_err_t1": _rel_inf(h1.cpu().numpy()[0], r1c["h"][0]), "path": "hybrid (last replayed graph)"}
 
     rng_inst = synth.make_batch("dft", 8192, 64, 4, 256, snr_db=None, prec="fp32", seed=3)
     p3 = binding.Plan(8192, rng_inst["omega"], "dft", "fp32")
@@ -244,7 +334,7 @@ def secondary(args, dev, plan, inst, stream, flush):
                                   "paper_flop_model": costmodel.cosamp_fast_ratio(8192, 4)}
     out["large_dft_c64_N4194304_M524288"] = large_single(dev, stream, flush)
     out["serving"] = serving(args.serve_requests)
-    out["uneven_batch"] = uneven(args.uneven_instances)
+    out["uneven_batch"] = uneven(args.uneven_instances, refs.get("uneven") if refs else None)
     return out
 
 
@@ -252,7 +342,7 @@ def _uneven_gen(spec):
     return synth.uneven_instance(spec)
 
 
-def uneven(n_inst: int):
+def uneven(n_inst: int, refs=None):
     """The uneven batch: n_inst instances (4096 by default), N = 2^12 .. 2^16,
     M = N/4 or N/8, K = 8 .. 256, half partial WHT FP32 and half partial DFT
     complex64, each with its own Omega, +-1 or Gaussian nonzeros, noiseless;
@@ -284,11 +374,18 @@ def uneven(n_inst: int):
         times.append(e0.elapsed_time(e1))
     ms = statistics.median(times)
     iters = int(bt.iters.sum().item())
+    acc = None
+    if refs:
+        it_n, rn_n = bt.iters.cpu().numpy(), bt.resnorm.cpu().numpy()
+        rows = [compare_run(r, bt.supp[i].cpu().numpy(), it_n[i], bt.x[i].cpu().numpy(), rn_n[i])
+                for i, r in refs.items()]
+        acc = {"sample": f"{len(refs)} instances spread over the batch whose oracle run is short "
+                         "(M K^3/3 <= 2e9), transform oracle", **summarize(rows)}
     return {"workload": f"{n_inst} instances, N=2^12..2^16, M=N/4 or N/8, K=8..256, WHT fp32 / DFT c64, "
                         "per-instance Omega, noiseless", "call": "cs_omp_batched", "instances": n_inst,
             "plan_build_s": plan_s, "ms": ms, "solves_per_s": n_inst / ms * 1e3,
             "correlations_per_s": iters / ms * 1e3, "iterations": iters,
-            "device_error": plans[0].device_error()}
+            "device_error": plans[0].device_error(), "accuracy": acc}
 
 
 def huge_instance(N=1 << 22, M=1 << 19, K=4096):
@@ -434,15 +531,48 @@ def large_single(dev, stream, flush, N=1 << 22, M=1 << 19, K=256):
     return out
 
 
-def run_gpu(args, rank: int, world: int):
+def accuracy_batch(plan, inst, y_dev, outs, refs, t_switch: int):
+    """Errors of the timed step against the FP64 oracle on the SAMPLE
+    instances: supports, iteration counts, x and ||r||/||y|| of the hybrid
+    step's outputs; h at t = 1 (cs_correlate) and the kernel-sum correlation
+    with s = 1 .. K-1 columns (cs_correlate_fast on the GPU's own first s
+    columns and coefficients, which cs_omp with K = s returns), each as
+    l_inf / ||h||_inf against the oracle's h with s columns."""
     import torch
-    from paper_1205_4139_gb300 import binding
+    x, supp, iters, rn = (t.cpu().numpy() for t in outs)
+    rows = [compare_run(refs[i], supp[b], iters[b], x[b], rn[b]) for i, b in enumerate(SAMPLE)]
+    K = inst["K"]
+    ys = y_dev[torch.tensor(SAMPLE, device=y_dev.device)].contiguous()
+    h0, _ = plan.correlate(ys)
+    h0n = h0.cpu().numpy()
+    h_t1 = max(_rel_inf(h0n[i], refs[i]["h"][0]) for i in range(len(SAMPLE)))
+    per_s = {}
+    for s_ in range(1, K):
+        xs, sp, _, _ = plan.omp(ys, s_, path="fast")
+        h, _ = plan.correlate_fast(h0, sp, xs.to(h0.dtype).contiguous())
+        hn, spn = h.cpu().numpy(), sp.cpu().numpy()
+        errs = [_rel_inf(hn[i], refs[i]["h"][s_]) for i in range(len(SAMPLE))
+                if len(refs[i]["h"]) > s_ and spn[i].tolist() == list(refs[i]["support"][:s_])]
+        if errs:
+            per_s[s_] = max(errs)
+    s_sw = min(t_switch, K) - 1
+    return {"sample": f"{len(SAMPLE)} of the 1024 instances (indices {SAMPLE[0]}..{SAMPLE[-1]}, slots reused "
+                      "past 607)", **summarize(rows),
+            "h_err_t1": h_t1, "h_err_at_switch": per_s.get(s_sw), "switch_atoms": s_sw,
+            "h_err_kernel_sum_max": max(per_s.values()) if per_s else None,
+            "h_err_kernel_sum_worst_s": max(per_s, key=per_s.get) if per_s else None,
+            "h_err_definition": "l_inf(h_gpu - h_oracle) / l_inf(h_oracle), same columns and the GPU's coefficients"}
+
+
+def run_gpu(args, rank: int, world: int, refs=None):
+    import torch
+    from paper_1205_4139_gb300 import binding, replicas
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     cfg = dict(CFG)
     B, N, M, K = cfg["B"], cfg["N"], cfg["M"], cfg["K"]
-    cfg["seed"] = rank * B              # rank r solves instances seeded r*B+1 .. r*B+B
+    cfg["seed"] = replicas.shard_seed(rank, B)  # rank r solves global instances r*B .. r*B+B-1
     inst = synth.make_batch(**{**cfg, "omega_seed": 0})
 
     t0 = time.perf_counter()
@@ -517,14 +647,15 @@ def run_gpu(args, rank: int, world: int):
     h2d = y.numel() * y.element_size()
     d2h = sum(t.numel() * t.element_size() for t in (x, supp, iters, rn))
 
-    extra = secondary(args, dev, plan, inst, stream, flush) if (rank == 0 and not args.no_extra) else {}
+    acc = None
+    if rank == 0 and refs is not None and refs.get("config2") is not None:
+        step("hybrid", -1)
+        acc = accuracy_batch(plan, inst, y, (x, supp, iters, rn), refs["config2"], best_ts)
+    extra = secondary(args, dev, plan, inst, stream, flush, refs) if (rank == 0 and not args.no_extra) else {}
 
     # max over ranks
-    vals = torch.tensor([total_ms, sum(e2e_ms) / len(e2e_ms), statistics.median(fast_ms),
-                         statistics.median(conv_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-    total_ms, e2e_mean, fast_med, conv_med = vals.tolist()
+    total_ms, e2e_mean, fast_med, conv_med = replicas.max_over_ranks(
+        [total_ms, sum(e2e_ms) / len(e2e_ms), statistics.median(fast_ms), statistics.median(conv_ms)], dev)
 
     flops = correlation_flops(N, it_np, best_ts, "hybrid")
     per_launch_ms = total_ms / args.steps
@@ -546,6 +677,7 @@ def run_gpu(args, rank: int, world: int):
         "clocks": clk.summary(),
         "gpu_launches": args.steps,
         "iters_mean": float(it_np.mean()),
+        "accuracy": acc,
         "extra": extra,
     }
 
@@ -556,7 +688,6 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle instances (default one per core)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement")
     ap.add_argument("--uneven-instances", type=int, default=4096, help="instances of the uneven-batch measurement")
     ap.add_argument("--huge", action="store_true",
@@ -567,7 +698,6 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     cores = len(os.sched_getaffinity(0))
-    n_cpu = args.cpu_sample or cores
 
     if args.huge:
         print(json.dumps(huge_instance()))
@@ -581,10 +711,10 @@ def main():
         inst = synth.make_batch(**{**CFG, "B": cores})
         budget_s, t_start = 150.0, time.perf_counter()
         for _ in range(min(args.warmup, 3)):
-            oracle_throughput(inst, cores, cores)
+            oracle_throughput(inst, range(cores), cores)
         vals = []
         while len(vals) < args.steps and (not vals or time.perf_counter() - t_start < budget_s):
-            vals.append(oracle_throughput(inst, cores, cores)[0])
+            vals.append(oracle_throughput(inst, range(cores), cores)[0])
         v = statistics.median(vals)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
                 "steps": len(vals), "steps_requested": args.steps, "warmup": args.warmup,
@@ -601,17 +731,21 @@ def main():
         return
 
     # CPU baseline first (spawned pool, before any GPU call), rank 0 at N=1 only
-    cpu = None
+    cpu, refs = None, None
     if rank == 0 and world == 1:
         inst0 = synth.make_batch(**CFG)
-        v, dt = oracle_throughput(inst0, n_cpu, cores)
+        v, dt, res = oracle_throughput(inst0, SAMPLE, cores, record=True)
         cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
-               "sample": f"{n_cpu} of the 1024 instances, FP64 dense Algorithm 1.1, {dt:.1f} s wall"}
+               "sample": f"{len(SAMPLE)} of the 1024 instances (indices {SAMPLE[0]}..{SAMPLE[-1]}), FP64 dense "
+                         f"Algorithm 1.1, {dt:.1f} s wall"}
+        refs = {"config2": res}
+        if not args.no_extra:
+            refs.update(oracle_refs(cores, args.uneven_instances))
 
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    r = run_gpu(args, rank, world)
+    r = run_gpu(args, rank, world, refs)
     if rank == 0:
         line = {"metric": METRIC, "value": r["value"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
@@ -623,7 +757,8 @@ def main():
                 "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "correlations_per_s": r["correlations_per_s"],
                 "fast": r["fast"], "conv": r["conv"], "plan_ms": r["plan_ms"],
                 "t_switch_default": r["t_switch_default"], "t_switch_sweep_ms": r["t_switch_sweep_ms"],
-                "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
+                "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "accuracy": r["accuracy"],
+                "clocks": r["clocks"],
                 "gpu_launches": r["gpu_launches"], "secondary": r["extra"]}
         print(json.dumps(line))
     if world > 1:

@@ -206,7 +206,9 @@ cs_status cs_omp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, co
  *   iters_dev, resnorm_dev  device arrays [count], indexed by b (each NULL
  *              allowed)
  * halt as in cs_omp; with t_switch < 0 an instance takes its plan's switch
- * point (N <= 8192) or 32 (larger N: their kernel sums stream c through L2).
+ * point (cs_plan_switch) for N <= 8192, 32 for 8192 < N <= 2^16 (their
+ * kernel sums stream c through L2), and its plan's switch point again (tuned,
+ * else the GB300 table) for N > 2^16.
  * Instances with N <= 8192 give bit for bit the results of cs_omp on their
  * plan.  Those with 8192 < N <= 2^16 run the one-CTA radix-16 chains on
  * vectors in global memory, two passes per round trip through a
@@ -261,9 +263,14 @@ cs_status cs_cosamp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K,
  *   - The first call on a device looks up that array's device address with
  *     cudaGetSymbolAddress (with the device current) and caches it; make that
  *     first call before any stream capture.
- *   - If one CTA's share (N working elements + K(K+1)/2 FP64 elements + 16
- *     bytes) exceeds 32 MiB the call returns CS_ERR_UNSUPPORTED with a message
- *     in cs_last_error; otherwise it runs as many resident CTAs as fit.
+ *   - One CTA runs two instances at a time; its share of the array is
+ *     2N working elements (sizeof F each) plus 2 K(K+1)/2 factor entries (16
+ *     bytes each for DFT, 8 for WHT), each part rounded up to 16 bytes, plus
+ *     16 bytes.  If one CTA's share exceeds 32 MiB the call returns
+ *     CS_ERR_UNSUPPORTED with a message in cs_last_error; otherwise it runs
+ *     as many resident CTAs as fit.
+ *   - t_switch < 0 takes the plan's switch point (cs_plan_switch), as cs_omp
+ *     does.
  *   - Every call on a device shares the array and leaves its contents behind;
  *     the call clears what must start at zero.  Calls that overlap on the GPU
  *     (other streams, other threads, other plans) race on it: serialise them.

@@ -105,12 +105,11 @@ cudaError_t fork_stream(int dev, int k, cudaStream_t* out) {
 
 // accessors for the other translation units of the library
 const PlanView* plan_view(cs_plan_t plan) { return &plan->v; }
-int plan_t_switch_default(cs_plan_t plan) { return plan->t_switch_default; }
 void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 }  // namespace csf
 
 // Crossover of the two correlations measured on GB300 (python -m
-// paper_1205_4139_gb300.switch_curves: OMP per-iteration cost of kernel sums
+// switch_curves.py: OMP per-iteration cost of kernel sums
 // and of transforms versus t, M = N/4, partial DFT and WHT): the t above
 // which transforms are cheaper per iteration, by log2 N.  One-CTA plans
 // (batches of instances in shared memory) cross near 64.  A large plan (one
@@ -132,6 +131,11 @@ static int gb300_switch(int logN) {
 static int plan_switch(const cs_plan_s* p) {
   return p->t_switch_tuned >= 0 ? p->t_switch_tuned : gb300_switch(p->v.logN);
 }
+
+namespace csf {
+// the switch point of calls with t_switch < 0, for the other translation units
+int plan_switch_point(cs_plan_t plan) { return plan_switch(plan); }
+}  // namespace csf
 
 static void plan_free(cs_plan_s* p) {
   if (!p) return;

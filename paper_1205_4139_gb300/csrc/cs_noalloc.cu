@@ -38,7 +38,7 @@ thread_local char g_noalloc_err[256] = "";
 // Per-plan accessors exported by cs_api.cu for this file.
 namespace csf {
 const PlanView* plan_view(cs_plan_t plan);
-int plan_t_switch_default(cs_plan_t plan);
+int plan_switch_point(cs_plan_t plan);
 void set_last_error(const char* msg);
 }  // namespace csf
 
@@ -113,7 +113,8 @@ extern "C" cs_status cs_omp_noalloc(cs_plan_t plan, const void* y_dev, int64_t b
   a.K = K;
   a.rel_tol = h.rel_tol;
   a.path = h.path;
-  a.t_switch = h.t_switch < 0 ? plan_t_switch_default(plan) : h.t_switch;
+  // the same switch point as cs_omp: cs_plan_tune's, else the GB300 table
+  a.t_switch = h.t_switch < 0 ? plan_switch_point(plan) : h.t_switch;
   a.x_out = x_dev;
   a.supp_out = supp_dev;
   a.iters_out = iters_dev;

@@ -7,14 +7,14 @@ first `count` instances of one kind (wht / dft / all) and residence (small:
 N <= 8192, big: larger N, all) of the 4096-instance uneven batch, in two
 cs_omp_batched calls (the second is the one to capture).
 
-  python -m paper_1205_4139_gb300.profile_case [batch]
-  python -m paper_1205_4139_gb300.profile_case 1 single
-  python -m paper_1205_4139_gb300.profile_case uneven dft big 304
+  python profile_case.py [batch]
+  python profile_case.py 1 single
+  python profile_case.py uneven dft big 304
 """
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -5,12 +5,12 @@ by transforms on one measurement (residual and adjoint passes, the
 least-squares kernel): the case the committed ncu summaries of the large path
 capture.
 
-  python -m paper_1205_4139_gb300.profile_large [batch]
+  python profile_large.py [batch]
 """
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -4,13 +4,13 @@ timed with K = k for a ladder of k on the kernel-sum path (FAST) and on the
 transform path (CONV); the slope between consecutive k is the cost of one
 iteration at t ~ k.  Prints one JSON line per (kind, precision, N).
 
-  python -m paper_1205_4139_gb300.switch_curves [logN ...]
+  python switch_curves.py [logN ...]
 """
 import json
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
