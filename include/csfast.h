@@ -175,7 +175,12 @@ cs_status cs_correlate_fast(cs_plan_t plan, const void* h0_dev, const int32_t* s
  *   iters_dev  int32: number of selected columns
  *   resnorm_dev double: ||r|| / ||y|| at exit (0 for y = 0), from the FP64
  *              downdate ||r_t||^2 = ||y||^2 - sum |z_k|^2 of the Cholesky
- *              update
+ *              update, or in FP32 mode, once that downdate falls below
+ *              1e-5 ||y||^2, from the explicit residual y - Phi x (one
+ *              forward transform, FP64 accumulation), on which the
+ *              tolerance test is then decided: the FP32 right-hand side
+ *              leaves about 1e-7 ||y||^2 of rounding in the downdate, the
+ *              explicit residual resolves ||r||/||y|| to a few 1e-7
  * Any output pointer except supp_dev may be NULL (supp_dev too when K = 0).  halt may be NULL
  * (rel_tol 1e-6, hybrid path, default switch).  Limits: 0 <= K <= min(M, 1024)
  * for N <= 8192, 0 <= K <= min(M, 4096) for larger plans. */

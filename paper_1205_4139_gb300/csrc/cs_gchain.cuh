@@ -57,15 +57,18 @@ struct ZeroFillLoad {
 
 // N^{-1/2} y - N^{-1} (F x) on Omega and 0 elsewhere, stored to the vector:
 // the zero-filled residual of step 7 from the forward transform of x.
-template <class E>
+template <class E, bool NORM = false>
 struct ResidualSink {
   const int* slot;
   const E* y;
   typename FT<E>::R sy, sx;
   E* out;
+  double acc = 0.0;  // with NORM: this thread's share of sum |out|^2 (FP64)
   __device__ __forceinline__ void operator()(int pos, const E& fx) {
     const int m = __ldg(slot + pos);
-    out[pos] = m >= 0 ? sub(scale(y[m], sy), scale(fx, sx)) : zero<E>();
+    const E r = m >= 0 ? sub(scale(y[m], sy), scale(fx, sx)) : zero<E>();
+    if constexpr (NORM) acc += norm2(to_w(r));
+    out[pos] = r;
   }
 };
 
@@ -287,20 +290,42 @@ __device__ int gcorrelate_transform(const Grp& g, E* gbuf, E* tile, const E* tws
 // correlate_residual): forward chain from the sparse coefficients whose last
 // stage writes the masked residual, adjoint chain whose last stage feeds the
 // arg-max over j not in Lambda.
-template <class E, bool DFT>
+// With NORM, *r2 receives ||y - Phi x||^2 (FP64 accumulation of the
+// working-precision residual; red holds 33 doubles).
+template <class E, bool DFT, bool NORM = false>
 __device__ int gcorrelate_residual(const Grp& g, E* gbuf, E* tile, const E* tws, const PlanDev<E>& P,
                                    const E* __restrict__ y,
                                    const uint32_t* bits, const uint16_t* kidx, const E* xw,
-                                   typename NormT<E>::V* rv, int* rj) {
+                                   typename NormT<E>::V* rv, int* rj, double* r2 = nullptr, double* red = nullptr) {
   using R = typename FT<E>::R;
   using V = typename NormT<E>::V;
   const SparseLoader<E> sl{bits, kidx, xw};
-  ResidualSink<E> rs{P.slot, y, inv_sqrt_pow2<R>(P.logN), (R)1 / (R)P.N, gbuf};
+  ResidualSink<E, NORM> rs{P.slot, y, inv_sqrt_pow2<R>(P.logN), (R)1 / (R)P.N, gbuf};
   gchain<DFT ? 0 : 2>(g, gbuf, tile, P.logN, P.tw, tws, sl, rs);
+  if constexpr (NORM) {
+    double acc[1] = {rs.acc};
+    group_sum(g, acc, red);
+    *r2 = acc[0] * (double)P.N;  // the entries are r_m / sqrt(N)
+  }
   NoLoad nl;
   ArgmaxSink<E> sk{bits, nullptr, (V)-1, 0x7fffffff, nullptr};
   gchain<DFT ? 1 : 2>(g, gbuf, tile, P.logN, P.tw, tws, nl, sk);
   return group_argmax(g, sk.bv, sk.bj, rv, rj);
+}
+
+// ||y - Phi x||^2 for a vector in global memory: the forward chain of
+// gcorrelate_residual with its residual sink, without the adjoint.
+template <class E, bool DFT>
+__device__ double gresidual_norm(const Grp& g, E* gbuf, E* tile, const E* tws, const PlanDev<E>& P,
+                                 const E* __restrict__ y, const uint32_t* bits, const uint16_t* kidx, const E* xw,
+                                 double* red) {
+  using R = typename FT<E>::R;
+  const SparseLoader<E> sl{bits, kidx, xw};
+  ResidualSink<E, true> rs{P.slot, y, inv_sqrt_pow2<R>(P.logN), (R)1 / (R)P.N, gbuf};
+  gchain<DFT ? 0 : 2>(g, gbuf, tile, P.logN, P.tw, tws, sl, rs);
+  double acc[1] = {rs.acc};
+  group_sum(g, acc, red);
+  return acc[0] * (double)P.N;
 }
 
 }  // namespace csf

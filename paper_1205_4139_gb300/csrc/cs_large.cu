@@ -98,7 +98,8 @@ template <class E> __host__ __device__ inline int lstride(int len) { return len 
 struct LState {  // per instance, in the workspace
   int p, done, pad0, pad1;
   double ynorm2, rn2;
-  int ncols, pad2;  // distinct support columns of the four-step split registered so far
+  int ncols;  // distinct support columns of the four-step split registered so far
+  int chk;    // FP32 mode: the halting test waits for the explicit residual (lchk_kernel)
 };
 
 // Compact input of pass 2 for a sparse vector (the forward transform of
@@ -112,7 +113,7 @@ struct LSparse {
 };
 
 enum { LD_DENSE = 0, LD_ZF = 1, LD_ONES = 2 };
-enum { SK_H = 0, SK_ARG = 1, SK_RES = 2, SK_KV = 3 };
+enum { SK_H = 0, SK_ARG = 1, SK_RES = 2, SK_KV = 3, SK_RESN = 4 };
 
 template <class E> __device__ __forceinline__ E one_e();
 template <> __device__ __forceinline__ float one_e<float>() { return 1.f; }
@@ -290,6 +291,9 @@ __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restric
 //   SK_ARG  arg-max over j whose bit is clear in `bits` -> partial
 //   SK_RES  out[j] = y[m] - v where j = Omega_m (other j untouched)
 //   SK_KV   out[j] = v
+//   SK_RESN only for instances whose state asks for the explicit residual:
+//           the CTA's FP64 share of sum |y[m] - v|^2 over Omega's members in
+//           its rows -> rpart[b * gridDim.x + blockIdx.x] (nothing stored)
 // A partial is written to part_v / part_j[b * nparts + blockIdx.x].
 template <class E, bool DFT, int SK>
 __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restrict__ T, int neg,
@@ -297,13 +301,15 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
                                                    const E* __restrict__ y, const uint32_t* __restrict__ bits,
                                                    typename NormT<E>::V* __restrict__ part_v,
                                                    int* __restrict__ part_j, int nparts,
-                                                   const LState* __restrict__ st, LSparse<E> sp) {
+                                                   const LState* __restrict__ st, LSparse<E> sp,
+                                                   double* __restrict__ rpart) {
   using V = typename NormT<E>::V;
   constexpr int C = tile_c<E>(), LC = log_tile_c<E>();
   extern __shared__ __align__(16) unsigned char sm[];
   E* buf = (E*)sm;
   const int64_t b = blockIdx.y;
   if (st && st[b].done) return;
+  if (SK == SK_RESN && !st[b].chk) return;
   const int n1 = P.n1, n2 = P.n2, N2 = 1 << n2, Nm = P.N - 1;
   const int cs = lstride<E>(N2);
   const PassSmem<E> L = pass_layout<E>(N2);
@@ -336,6 +342,29 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
   E* dst = out ? out + b * (int64_t)P.N : nullptr;
   const E* yb = y ? y + b * (int64_t)P.M : nullptr;
   const uint32_t* bb = bits ? bits + b * (int64_t)(P.N >> 5) : nullptr;
+  if constexpr (SK == SK_RESN) {  // ||y - Phi x||^2, this CTA's share, FP64, fixed order
+    __shared__ double red[kLT / 32];
+    double acc = 0.0;
+    if (P.om_off) {
+      const int e0 = __ldg(P.om_off + r0), e1 = __ldg(P.om_off + r0 + C);
+      for (int e = e0 + (int)threadIdx.x; e < e1; e += kLT) {
+        const int2 jm = __ldg(P.om_ent + e);  // (j, m)
+        const int j = jm.x;
+        int c, pos;
+        if constexpr (DFT) {
+          c = (j & ((1 << n1) - 1)) - r0;
+          pos = tab[j >> n1];
+        } else {
+          c = (j >> n2) - r0;
+          pos = j & (N2 - 1);
+        }
+        acc += norm2(to_w(sub(yb[jm.y], scale(buf[c * cs + swz<E>(pos)], scl))));
+      }
+    }
+    acc = block_sum0(acc, red);
+    if (threadIdx.x == 0) rpart[b * gridDim.x + blockIdx.x] = acc;
+    return;
+  }
   if constexpr (SK == SK_RES) {
     // only Omega's outputs are wanted: visit the members of Omega in this
     // CTA's rows (grouped by row in the plan) instead of every output's slot
@@ -427,9 +456,9 @@ template <class E, bool DFT>
 __global__ void __launch_bounds__(kLT) lsp1_kernel(LDev<E> P, const E* __restrict__ xw, const int* __restrict__ lam,
                                                    const int* __restrict__ chead, const int* __restrict__ cnext,
                                                    int K, int kc, int kcl, E* __restrict__ Tc,
-                                                   const LState* __restrict__ st) {
+                                                   const LState* __restrict__ st, int only_chk) {
   const int64_t b = blockIdx.y;
-  if (st[b].done) return;
+  if (st[b].done || (only_chk && !st[b].chk)) return;
   const int nc = st[b].ncols;
   const int N1 = 1 << P.n1;
   const int idx = blockIdx.x * kLT + threadIdx.x;
@@ -897,13 +926,44 @@ __device__ void ls_w_phase(const LOmpArgs<E>& a, int G, int gi, int64_t b) {
   __syncthreads();
   if (ticket != G - 1) return;
   __threadfence();
-  if (p + 1 >= K || rn2 < a.rel_tol * a.rel_tol * ynorm2) {
+  // step 8; in FP32 mode a downdate near the tolerance leaves the decision to
+  // lchk_kernel, which forms the explicit residual
+  const bool chk = resid_check<E>(a.rel_tol) && rn2 < kResidTrigger * ynorm2;
+  if (!chk && (p + 1 >= K || rn2 < a.rel_tol * a.rel_tol * ynorm2)) {
     lwrite_outputs(a, b, p + 1, ynorm2, rn2);
   } else if (threadIdx.x == 0) {
     S->p = p + 1;
     S->rn2 = rn2;
+    S->chk = chk ? 1 : 0;
   }
   if (threadIdx.x == 0) S->pad0 = 0;
+}
+
+// The halting test on the explicit residual (FP32 mode), one CTA per
+// instance after the SK_RESN pass: ||r||^2 from the pass's nparts shares in a
+// fixed order; stop when ||r|| < rel_tol ||y|| or K columns are in, else
+// continue from the explicit value.
+template <class E>
+__global__ void __launch_bounds__(kLT) lchk_kernel(LOmpArgs<E> a, const double* __restrict__ rpart, int nparts) {
+  __shared__ double red[kLT / 32];
+  const int64_t b = blockIdx.y;
+  LState* S = a.st + b;
+  if (S->done || !S->chk) return;
+  double t = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += kLT) t += rpart[b * nparts + i];
+  t = block_sum0(t, red);
+  __syncthreads();
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  const double r2 = red[0], ynorm2 = S->ynorm2;
+  const int p = S->p;
+  __syncthreads();  // every thread has read the state
+  if (p >= a.K || r2 < a.rel_tol * a.rel_tol * ynorm2) {
+    lwrite_outputs(a, b, p, ynorm2, r2);
+  } else if (threadIdx.x == 0) {
+    S->rn2 = r2;
+    S->chk = 0;
+  }
 }
 
 // grid (G, batch); dynamic smem: K FP64 elements (the Gram column g)
@@ -959,13 +1019,13 @@ cudaError_t run_col(const LDev<E>& P, const E* in, int64_t in_stride, E* out, co
 template <class E, bool DFT, int SK>
 cudaError_t run_row(const LDev<E>& P, const E* T, int neg, double scl, E* out, const E* y, const uint32_t* bits,
                     typename NormT<E>::V* pv, int* pj, int nparts, const LState* st, int64_t batch,
-                    cudaStream_t s, LSparse<E> sp = LSparse<E>{nullptr, nullptr, 0}) {
+                    cudaStream_t s, LSparse<E> sp = LSparse<E>{nullptr, nullptr, 0}, double* rpart = nullptr) {
   const size_t smem = pass_layout<E>(1 << P.n2).total;
   cudaError_t e = allow_smem(lrow_kernel<E, DFT, SK>, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((1u << P.n1) / tile_c<E>(), (unsigned)batch);
   lrow_kernel<E, DFT, SK><<<grid, kLT, smem, s>>>(P, T, neg, (typename FT<E>::R)scl, out, y, bits, pv, pj,
-                                                  nparts, st, sp);
+                                                  nparts, st, sp, rpart);
   return cudaGetLastError();
 }
 
@@ -1098,7 +1158,7 @@ cudaError_t fast_t(const PlanView& Pv, const void* h0, const int32_t* supp, cons
 // ------------------------------------------------------------------- OMP
 template <class E>
 struct LOmpWs {
-  size_t st, h0, T, Z, xz, bits, B, z, x, u, xw, lam, pv, pj, yp, tm, cm, cl, ch, ct, cn, Tc, total;
+  size_t st, h0, T, Z, xz, bits, B, z, x, u, xw, lam, pv, pj, yp, tm, cm, cl, ch, ct, cn, Tc, rp, total;
   int nparts, nyp, gmax, kc;
 };
 
@@ -1140,9 +1200,11 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
     L.gmax = (int)(g < 1 ? 1 : (g > 256 ? 256 : g));
   }
   L.tm = o;   o = al16(o + (size_t)batch * L.gmax * 3 * sizeof(double));
-  // the sparse pass 1 of the transform path: registered support columns,
-  // kc = min(K, N2) of them (a support never spans more than N2 columns)
-  L.kc = conv ? (K < (1 << P.n2) ? K : (1 << P.n2)) : 0;
+  // the sparse pass 1 of the transform path (and of the explicit residual
+  // of FP32 mode): registered support columns, kc = min(K, N2) of them (a
+  // support never spans more than N2 columns)
+  const bool fp32 = sizeof(typename FT<E>::R) == 4;
+  L.kc = (conv || fp32) ? (K < (1 << P.n2) ? K : (1 << P.n2)) : 0;
   const size_t kcs = (size_t)L.kc;
   L.cm = o;   o = al16(o + (kcs ? (size_t)batch * ((size_t)1 << P.n2) * sizeof(int) : 0));
   L.cl = o;   o = al16(o + (size_t)batch * kcs * sizeof(int));
@@ -1150,6 +1212,7 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
   L.ct = o;   o = al16(o + (size_t)batch * kcs * sizeof(int));
   L.cn = o;   o = al16(o + (kcs ? (size_t)batch * Kc * sizeof(int) : 0));
   L.Tc = o;   o = al16(o + (size_t)batch * ((size_t)1 << P.n1) * kcs * sizeof(E));
+  L.rp = o;   o = al16(o + (fp32 ? (size_t)batch * row_parts(P) * sizeof(double) : 0));  // SK_RESN shares
   L.total = o;
   return L;
 }
@@ -1198,6 +1261,8 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
   A.ctail = (int*)(w + L.ct);
   A.cnext = (int*)(w + L.cn);
   E* Tc = (E*)(w + L.Tc);
+  double* rpart = (double*)(w + L.rp);
+  const bool chk_mode = resid_check<E>(a.rel_tol) && a.K > 0;
   const size_t Nv = (size_t)batch * P.N * sizeof(E);
   cudaError_t e;
   if ((e = cudaMemsetAsync(A.st, 0, (size_t)batch * sizeof(LState), s)) != cudaSuccess) return e;
@@ -1230,7 +1295,7 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
               // pass 1 from the support's columns, pass 2 from the compact result
       const int N1 = 1 << P.n1, kcl = (t - 1) < L.kc ? (t - 1) : L.kc;
       const dim3 g1((unsigned)(((int64_t)N1 * kcl + kLT - 1) / kLT), (unsigned)batch);
-      lsp1_kernel<E, DFT><<<g1, kLT, 0, s>>>(P, A.xw, A.lam, A.chead, A.cnext, a.K, L.kc, kcl, Tc, A.st);
+      lsp1_kernel<E, DFT><<<g1, kLT, 0, s>>>(P, A.xw, A.lam, A.chead, A.cnext, a.K, L.kc, kcl, Tc, A.st, 0);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_RES>(P, nullptr, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s,
                                        LSparse<E>{Tc, A.cols, L.kc})) != cudaSuccess)
@@ -1250,6 +1315,17 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
       lls_w_kernel<E><<<lg, kLT, 0, s>>>(A);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (chk_mode) {  // the explicit residual of instances whose downdate neared the tolerance
+      const int N1 = 1 << P.n1, kcl = t < L.kc ? t : L.kc;
+      const dim3 g1((unsigned)(((int64_t)N1 * kcl + kLT - 1) / kLT), (unsigned)batch);
+      lsp1_kernel<E, DFT><<<g1, kLT, 0, s>>>(P, A.xw, A.lam, A.chead, A.cnext, a.K, L.kc, kcl, Tc, A.st, 1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = run_row<E, DFT, SK_RESN>(P, nullptr, 0, isq, nullptr, A.y, nullptr, nullptr, nullptr, 0, A.st, batch,
+                                        s, LSparse<E>{Tc, A.cols, L.kc}, rpart)) != cudaSuccess)
+        return e;
+      lchk_kernel<E><<<dim3(1, (unsigned)batch), kLT, 0, s>>>(A, rpart, rp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }

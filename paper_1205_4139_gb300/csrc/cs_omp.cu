@@ -92,7 +92,7 @@ __host__ __device__ inline OmpLayout<E> omp_layout(int N, int K, int path) {
 
 struct SlotState {
   int64_t b;
-  int p, lnew, state, pad;
+  int p, lnew, state, chk;  // chk: the next correlation step first checks the explicit residual
   double ynorm2, rn2;
 };
 
@@ -178,6 +178,7 @@ __device__ void corr_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const
     if (g.tid == 0) {
       S.lnew = l;
       S.p = 0;
+      S.chk = 0;
       S.ynorm2 = yy[0];
       S.rn2 = yy[0];
       S.state = NEED_LS;
@@ -188,6 +189,36 @@ __device__ void corr_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const
   const int p = S.p, t = p + 1;
   const bool fast = a.path == PATH_FAST || (a.path == PATH_HYBRID && t <= a.t_switch);
   int l;
+  if (S.chk) {  // halting test of step 8 on the explicit residual (FP32 mode)
+    const bool last = p >= a.K;
+    double r2;
+    if (!last && !fast) {  // the transform path forms the residual anyway
+      l = correlate_residual<E, DFT, true>(g, regA, a.P, a.y + S.b * M, v.bits, v.kidx, v.xw, rv, rj, nullptr,
+                                           nullptr, &r2, red);
+    } else {
+      r2 = residual_on_omega<E, DFT, true>(g, regA, a.P, a.y + S.b * M, v.bits, v.kidx, v.xw, red);
+    }
+    if (g.tid == 0) c_valid = 0;
+    const double ynorm2 = S.ynorm2;
+    if (last || r2 < a.rel_tol * a.rel_tol * ynorm2) {
+      write_outputs(g, a, v, S.b, p, ynorm2, r2);
+      g.sync();
+      if (g.tid == 0) S.state = NEED_INIT;
+      return;
+    }
+    g.sync();  // every thread has read S before it changes
+    if (g.tid == 0) {
+      S.rn2 = r2;
+      S.chk = 0;
+    }
+    if (!fast) {
+      if (g.tid == 0) {
+        S.lnew = l;
+        S.state = NEED_LS;
+      }
+      return;
+    }
+  }
   if (fast) {
     if (!c_valid) {
       load_kernel_vector<E, DFT>(g, regA, a.P, dbl);
@@ -237,7 +268,10 @@ __device__ void ls_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const S
     if (g.tid == 0) S.state = NEED_INIT;
     return;
   }
-  if (p + 1 >= K || S.rn2 < a.rel_tol * a.rel_tol * ynorm2) {  // step 8
+  // step 8: in FP32 mode a downdate near the tolerance defers the test to
+  // the explicit residual, which the next correlation step forms
+  const bool chk = resid_check<E>(a.rel_tol) && S.rn2 < kResidTrigger * ynorm2;
+  if (!chk && (p + 1 >= K || S.rn2 < a.rel_tol * a.rel_tol * ynorm2)) {
     write_outputs(g, a, v, b, p + 1, ynorm2, S.rn2);
     g.sync();
     if (g.tid == 0) S.state = NEED_INIT;
@@ -246,6 +280,7 @@ __device__ void ls_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const S
   g.sync();  // every thread has read S.rn2 before it is next written
   if (g.tid == 0) {
     S.p = p + 1;
+    S.chk = chk;
     S.state = NEED_CORR;
   }
 }
@@ -274,7 +309,7 @@ __global__ void __launch_bounds__(kOmpThreads, (sizeof(E) > 8 ? 1 : 2)) omp_kern
     const bool done = S[0].state == RETIRED && S[1].state == RETIRED;
     __syncthreads();  // every thread has read the states before any step changes them
     if (done) break;
-    // Every instance needs at most 2K + 4 phases of its slot and a CTA serves
+    // Every instance needs at most 2K + 6 phases of its slot and a CTA serves
     // at most the whole batch, so reaching the bound means a broken state
     // machine: record it in the status word and stop instead of spinning.
     if (phase >= a.max_phases) {
@@ -334,7 +369,7 @@ cudaError_t omp_impl(const PlanView& P, const OmpLaunch& L, void* ws, int grid, 
   char* w = (char*)ws;
   a.counter = (int*)w;
   a.status = P.status;
-  a.max_phases = 2 * (L.batch + 2) * (2LL * L.K + 6) + 16;
+  a.max_phases = 2 * (L.batch + 2) * (2LL * L.K + 10) + 16;
   a.h0_ws = (E*)(w + 16);
   a.B_ws = (W*)(w + 16 + a16((size_t)grid * 2 * P.N * sizeof(E)));
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);

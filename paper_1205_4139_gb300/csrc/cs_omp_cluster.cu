@@ -157,7 +157,10 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kQT) omp_cluster_k
       if (r == 0) q_outputs(a, b, lv.x, lv.lam, p, ynorm2, rn2_s);
       break;
     }
-    if (p + 1 >= K || rn2_s < a.rel_tol * a.rel_tol * ynorm2) {  // step 8
+    // step 8 (FP32 mode: a downdate near the tolerance defers the test to the
+    // explicit residual, as in the persistent kernel)
+    const bool chk = resid_check<E>(a.rel_tol) && rn2_s < kResidTrigger * ynorm2;
+    if (!chk && (p + 1 >= K || rn2_s < a.rel_tol * a.rel_tol * ynorm2)) {
       if (r == 0) q_outputs(a, b, lv.x, lv.lam, p + 1, ynorm2, rn2_s);
       break;
     }
@@ -165,6 +168,28 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kQT) omp_cluster_k
     p += 1;
     const int t = p + 1;
     const bool fast = a.path == PATH_FAST || (a.path == PATH_HYBRID && t <= a.t_switch);
+    if (chk) {  // every CTA forms the same residual and takes the same decision
+      const bool last = p >= K;
+      double r2;
+      int lr = -1;
+      if (!last && !fast) {
+        lr = correlate_residual<E, DFT, true>(gA, regA, a.P, y, lv.bits, lv.kidx, lv.xw, rv, rj, nullptr, nullptr,
+                                              &r2, red);
+      } else {
+        r2 = residual_on_omega<E, DFT, true>(gA, regA, a.P, y, lv.bits, lv.kidx, lv.xw, red);
+      }
+      c_valid = 0;
+      if (last || r2 < a.rel_tol * a.rel_tol * ynorm2) {
+        if (r == 0) q_outputs(a, b, lv.x, lv.lam, p, ynorm2, r2);
+        break;
+      }
+      if (threadIdx.x == 0) rn2_s = r2;
+      __syncthreads();
+      if (!fast) {
+        l = lr;
+        continue;
+      }
+    }
     if (fast) {
       if (!c_valid) {
         load_kernel_vector<E, DFT>(gA, regA, a.P, dbl);

@@ -115,7 +115,7 @@ template <class E>
 struct MSlot {
   MInst<E> I;
   int64_t b;
-  int p, lnew, state, pad;
+  int p, lnew, state, chk;  // chk: the next correlation step first checks the explicit residual
   double ynorm2, rn2;
 };
 
@@ -205,6 +205,7 @@ __device__ void mcorr_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, 
     if (g.tid == 0) {
       S.lnew = l;
       S.p = 0;
+      S.chk = 0;
       S.ynorm2 = yy[0];
       S.rn2 = yy[0];
       S.state = NEED_LS;
@@ -217,6 +218,36 @@ __device__ void mcorr_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, 
   const int p = S.p, t = p + 1, N = I.P.N;
   const bool fast = a.path == PATH_FAST || (a.path == PATH_HYBRID && t <= I.t_switch);
   int l;
+  if (S.chk) {  // halting test of step 8 on the explicit residual (FP32 mode), as in cs_omp
+    const bool last = p >= I.K;
+    double r2;
+    if (!last && !fast) {
+      l = correlate_residual<E, DFT, true>(g, v.buf, I.P, I.y, v.bits, v.kidx, v.xw, rv, rj, nullptr, nullptr, &r2,
+                                           red);
+    } else {
+      r2 = residual_on_omega<E, DFT, true>(g, v.buf, I.P, I.y, v.bits, v.kidx, v.xw, red);
+    }
+    if (g.tid == 0) ckey = nullptr;
+    const double ynorm2 = S.ynorm2;
+    if (last || r2 < a.rel_tol * a.rel_tol * ynorm2) {
+      mwrite(g, a, I, v, p, ynorm2, r2);
+      g.sync();
+      if (g.tid == 0) S.state = NEED_INIT;
+      return;
+    }
+    g.sync();  // every thread has read S before it changes
+    if (g.tid == 0) {
+      S.rn2 = r2;
+      S.chk = 0;
+    }
+    if (!fast) {
+      if (g.tid == 0) {
+        S.lnew = l;
+        S.state = NEED_LS;
+      }
+      return;
+    }
+  }
   if (fast) {
     E* regA = (E*)(sm + L.regA);
     const bool dbl = DFT && kernel_doubled<E>(N) && 2 * (size_t)N <= L.regA_n;
@@ -269,7 +300,10 @@ __device__ void mls_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, un
     if (g.tid == 0) S.state = NEED_INIT;
     return;
   }
-  if (p + 1 >= K || S.rn2 < a.rel_tol * a.rel_tol * ynorm2) {  // step 8
+  // step 8 (FP32 mode: a downdate near the tolerance defers the test to the
+  // explicit residual, which the next correlation step forms)
+  const bool chk = resid_check<E>(a.rel_tol) && S.rn2 < kResidTrigger * ynorm2;
+  if (!chk && (p + 1 >= K || S.rn2 < a.rel_tol * a.rel_tol * ynorm2)) {
     mwrite(g, a, I, v, p + 1, ynorm2, S.rn2);
     g.sync();
     if (g.tid == 0) S.state = NEED_INIT;
@@ -278,6 +312,7 @@ __device__ void mls_step(const Grp& g, const MArgs<E>& a, MSlot<E>& S, int s, un
   g.sync();  // every thread has read S.rn2 before it is next written
   if (g.tid == 0) {
     S.p = p + 1;
+    S.chk = chk;
     S.state = NEED_CORR;
   }
 }
@@ -431,8 +466,24 @@ __global__ void __launch_bounds__(kSThreads, seq_min_blocks<E>()) omp_seq_kernel
         ls_append(g, I.P, lv, h0, p, l, rn2, sh);            // step 6
         if (sh.st == 1) break;                              // column dependent on Lambda
         ++p;
-        if (p >= K || rn2 < a.rel_tol * a.rel_tol * ynorm2) break;  // step 8
+        // step 8 (FP32 mode: a downdate near the tolerance is decided on the
+        // explicit residual instead)
+        const bool chk = resid_check<E>(a.rel_tol) && rn2 < kResidTrigger * ynorm2;
+        if (!chk && (p >= K || rn2 < a.rel_tol * a.rel_tol * ynorm2)) break;
         const bool fast = a.path == PATH_FAST || (a.path == PATH_HYBRID && p + 1 <= I.t_switch);
+        if (chk) {
+          double r2;
+          if (p < K && !fast) {
+            l = gcorrelate_residual<E, DFT, true>(g, buf, tile, tws, I.P, I.y, lv.bits, lv.kidx, lv.xw, rv, rj, &r2,
+                                                  red);
+          } else {
+            r2 = gresidual_norm<E, DFT>(g, buf, tile, tws, I.P, I.y, lv.bits, lv.kidx, lv.xw, red);
+          }
+          if (g.tid == 0) rn2 = r2;  // every thread has read rn2 (the barriers of the chain)
+          g.sync();
+          if (p >= K || r2 < a.rel_tol * a.rel_tol * ynorm2) break;
+          if (!fast) continue;
+        }
         l = fast ? correlate_fast<E, DFT>(g, I.P.c, h0, lv.lam, lv.xw, p, N, lv.bits, nullptr, rv, rj, false)
                  : gcorrelate_residual<E, DFT>(g, buf, tile, tws, I.P, I.y, lv.bits, lv.kidx, lv.xw, rv, rj);
       }
@@ -546,7 +597,7 @@ cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int* ite
   a.kidx_ws = (uint16_t*)(ws + o_kidx);
   a.counter = (int*)ws;
   a.status = status;
-  a.max_phases = 2 * (n + 2) * (2LL * z.Kmax + 6) + 16;
+  a.max_phases = 2 * (n + 2) * (2LL * z.Kmax + 10) + 16;
   e = cudaMemsetAsync(ws, 0, 16, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ws + o_inst, d.data(), (size_t)n * sizeof(MInst<E>), cudaMemcpyHostToDevice, st);

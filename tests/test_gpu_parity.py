@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import synth
+from omp_checks import halting_ambiguous, resnorm_tol
 from oracle import kernelsum, matrices, omp as oomp
 
 torch = pytest.importorskip("torch")
@@ -148,17 +149,14 @@ def check_omp(inst, res, prec, noiseless, x_tol=None, check_all=True):
         got = supp[b][: iters[b]].tolist()
         assert got[:near] == ref["support"][:near], (b, near, got, ref["support"])
         if near == len(ref["gap"]):
-            assert iters[b] == ref["iters"], (b, iters[b], ref["iters"])
+            assert iters[b] == ref["iters"] or halting_ambiguous(ref, prec), (b, iters[b], ref["iters"])
             xr = np.asarray(ref["x"])
             err = np.max(np.abs(x[b][: len(xr)] - xr)) / np.max(np.abs(xr))
             tol = x_tol if x_tol is not None else (1e-10 if prec == "fp64" else 1e-4)
             assert err < tol, (b, err)
             assert np.all(supp[b][iters[b]:] == -1)
             rr = ref["resnorm"][-1] / ref["ynorm"]
-            # FP64: the downdate resolves ||r||/||y|| to ~1e-8; FP32: the
-            # right-hand side h_0 carries FP32 rounding, so ~1e-3 absolute
-            tol_r = 1e-6 * rr + 1e-7 if prec == "fp64" else max(1e-3 * rr, 1e-3)
-            assert abs(rn[b] - rr) <= tol_r, (b, rn[b], rr)
+            assert abs(rn[b] - rr) <= resnorm_tol(rr, prec), (b, rn[b], rr)
 
 
 @pytest.mark.parametrize("path", ["fast", "conv", "hybrid"])
