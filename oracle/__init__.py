@@ -13,9 +13,10 @@ Contents (each function cites the passage of the paper it follows):
                  Theorem 2-1 and the fast correlation of Eq. (kernelsum)
 * ``transform``  Algorithm 1.1 for large N with Phi applied through FFT / FWHT
                  (pinned against ``omp`` at N <= 4096)
-* ``pursuits``   subspace pursuit and CoSaMP in their standard forms (parity
-                 unpinned beyond recovery, OMP agreement on 1-sparse signals
-                 and least-squares optimality: the paper defines neither)
+* ``pursuits``   subspace pursuit and CoSaMP in their standard forms (the
+                 paper defines neither), pinned by iterates derived by hand
+                 for tiny cases, the invariants each step defines, recovery
+                 and OMP agreement on 1-sparse signals
 
 Everything is plain numpy in float64 / complex128 with no blocking, fusion or
 reordering beyond what the definitions state.

@@ -21,9 +21,12 @@ Readings (stated identically for the GPU path):
   otherwise accept, and stop when ||r|| < rel_tol ||y|| or after max_iter;
 * a zero measurement returns x = 0 with no iteration.
 
-Parity of these two functions is pinned only by recovery and invariants
-(exact noiseless recovery, agreement with OMP on 1-sparse signals, least
-squares optimality); the paper prints no iterate to compare against.
+Each run returns a trace of its iterations (SP: T', b, T_new, x_new and
+||r_new|| with the acceptance; CoSaMP: T, b, the kept set, x_new and ||r_new||
+with the acceptance).  The paper prints no iterate; the pins are iterates
+derived by hand for tiny cases (exact in binary arithmetic or with clear gaps
+between the k-th and (k+1)-th magnitudes), recovery, and the invariants each
+step defines (tests/test_oracle_pursuits.py).
 """
 from __future__ import annotations
 
@@ -72,6 +75,7 @@ def subspace_pursuit(Phi: np.ndarray, y: np.ndarray, K: int, max_iter: int | Non
     x = ls(Phi, y, T)
     rn = float(np.linalg.norm(_residual(Phi, y, T, x)))
     out["resnorm"] = [rn]
+    out["T0"], out["x0"], out["trace"] = T, x, []
     it = 0
     while it < max_iter and rn >= rel_tol * ynorm:
         r = _residual(Phi, y, T, x)
@@ -82,6 +86,7 @@ def subspace_pursuit(Phi: np.ndarray, y: np.ndarray, K: int, max_iter: int | Non
         xn = ls(Phi, y, Tn)
         rn_new = float(np.linalg.norm(_residual(Phi, y, Tn, xn)))
         it += 1
+        out["trace"].append({"Tp": Tp, "b": b, "Tn": Tn, "x": xn, "rn": rn_new, "accepted": rn_new < rn})
         if rn_new >= rn:
             break
         T, x, rn = Tn, xn, rn_new
@@ -101,6 +106,7 @@ def cosamp(Phi: np.ndarray, y: np.ndarray, K: int, max_iter: int = 50, rel_tol: 
     S = np.zeros(0, np.int64)
     x = np.zeros(0, y.dtype)
     rn = ynorm
+    out["trace"] = []
     it = 0
     while it < max_iter and rn >= rel_tol * ynorm:
         r = _residual(Phi, y, S, x)
@@ -111,6 +117,7 @@ def cosamp(Phi: np.ndarray, y: np.ndarray, K: int, max_iter: int = 50, rel_tol: 
         Sn, xn = T[keep], b[keep]
         rn_new = float(np.linalg.norm(_residual(Phi, y, Sn, xn)))
         it += 1
+        out["trace"].append({"T": T, "b": b, "S": Sn, "x": xn, "rn": rn_new, "accepted": rn_new < rn})
         if rn_new >= rn:
             break
         S, x, rn = Sn, xn, rn_new

@@ -113,3 +113,69 @@ def test_transform_residual_sign_is_caught(monkeypatch):
     orig = transform.synthesize
     monkeypatch.setattr(transform, "synthesize", lambda *a: -orig(*a))
     caught(tpins.test_omp_matches_dense_oracle, "wht", 1024, 256, 16, None)
+
+
+# ------------------------------------------------------ SP and CoSaMP
+import inspect  # noqa: E402
+import textwrap  # noqa: E402
+
+import tests.test_oracle_pursuits as ppins  # noqa: E402
+from oracle import pursuits  # noqa: E402
+
+
+def _plant(monkeypatch, name, old, new):
+    """Replace one statement of oracle.pursuits.<name> (the slip) and install
+    the changed function in the module."""
+    src = textwrap.dedent(inspect.getsource(getattr(pursuits, name)))
+    assert src.count(old) == 1, old
+    ns = dict(vars(pursuits))
+    exec(compile(src.replace(old, new), f"<{name} with a slip>", "exec"), ns)
+    monkeypatch.setattr(pursuits, name, ns[name])
+
+
+def _sp_pins():
+    for c in ppins.GOLD["sp"]:
+        ppins.test_sp_iterates_by_hand(c)
+    for kind in ppins.KINDS:
+        for seed in ppins.SP_SEEDS:
+            ppins.test_sp_steps_follow_their_definitions(kind, seed)
+
+
+def _cosamp_pins():
+    for c in ppins.GOLD["cosamp"]:
+        ppins.test_cosamp_iterates_by_hand(c)
+    for kind in ppins.KINDS:
+        for seed in ppins.COSAMP_SEEDS:
+            ppins.test_cosamp_steps_follow_their_definitions(kind, seed)
+
+
+def test_pins_pass_on_the_oracle():
+    _sp_pins()
+    _cosamp_pins()
+
+
+def test_sp_new_columns_over_all_j_is_caught(monkeypatch):
+    _plant(monkeypatch, "subspace_pursuit", "top_k(h, K, excluded=T)", "top_k(h, K)")
+    caught(_sp_pins)
+
+
+def test_cosamp_second_least_squares_is_caught(monkeypatch):
+    _plant(monkeypatch, "cosamp", "Sn, xn = T[keep], b[keep]", "Sn = T[keep]; xn = ls(Phi, y, Sn)")
+    caught(_cosamp_pins)
+
+
+def test_sp_accepting_an_equal_residual_is_caught(monkeypatch):
+    _plant(monkeypatch, "subspace_pursuit", "if rn_new >= rn:", "if rn_new > rn:")
+    caught(_sp_pins)
+
+
+def test_cosamp_keeping_a_rejected_iterate_is_caught(monkeypatch):
+    _plant(monkeypatch, "cosamp", "        if rn_new >= rn:\n            break\n        S, x, rn = Sn, xn, rn_new",
+           "        rn_prev = rn\n        S, x, rn = Sn, xn, rn_new\n        if rn_new >= rn_prev:\n            break")
+    caught(_cosamp_pins)
+
+
+def test_sp_keeping_a_rejected_iterate_is_caught(monkeypatch):
+    _plant(monkeypatch, "subspace_pursuit", "        if rn_new >= rn:\n            break\n        T, x, rn = Tn, xn, rn_new",
+           "        rn_prev = rn\n        T, x, rn = Tn, xn, rn_new\n        if rn_new >= rn_prev:\n            break")
+    caught(_sp_pins)

@@ -92,3 +92,147 @@ def test_zero_measurement():
     for f in (pursuits.subspace_pursuit, pursuits.cosamp):
         r = f(Phi, np.zeros(10, complex), 3)
         assert r["iters"] == 0 and len(r["support"]) == 0
+
+
+# ------------------------------------------------ iterates derived by hand
+import json  # noqa: E402
+import os  # noqa: E402
+from fractions import Fraction  # noqa: E402
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "pursuits_by_hand.json")))
+
+
+def _fr(v):
+    return float(Fraction(v[0], v[1]))
+
+
+def _case(c):
+    N, om = c["N"], np.array(c["omega"])
+    Phi = matrices.sensing(c["kind"], N, om)
+    xt = np.zeros(N)
+    for j, v in c["x_true"].items():
+        xt[int(j)] = _fr(v)
+    return Phi, Phi @ xt
+
+
+@pytest.mark.parametrize("case", GOLD["sp"], ids=lambda c: c["name"])
+def test_sp_iterates_by_hand(case):
+    Phi, y = _case(case)
+    res = pursuits.subspace_pursuit(Phi, y, case["K"])
+    assert res["T0"].tolist() == case["T0"]
+    assert np.allclose(res["x0"], [_fr(v) for v in case["x0"]], atol=1e-13)
+    assert np.isclose(res["resnorm"][0] ** 2, _fr(case["rn0_sq"]), atol=1e-13)
+    assert len(res["trace"]) == len(case["trace"])
+    for got, want in zip(res["trace"], case["trace"]):
+        assert got["Tp"].tolist() == want["Tp"] and got["Tn"].tolist() == want["Tn"]
+        assert np.allclose(got["b"], [_fr(v) for v in want["b"]], atol=1e-13)
+        assert np.allclose(got["x"], [_fr(v) for v in want["x"]], atol=1e-13)
+        assert np.isclose(got["rn"] ** 2, _fr(want["rn_sq"]), atol=1e-13)
+        assert got["accepted"] == want["accepted"]
+    assert res["support"].tolist() == case["support"] and res["iters"] == case["iters"]
+    assert np.allclose(res["x"], [_fr(v) for v in case["x"]], atol=1e-13)
+
+
+@pytest.mark.parametrize("case", GOLD["cosamp"], ids=lambda c: c["name"])
+def test_cosamp_iterates_by_hand(case):
+    Phi, y = _case(case)
+    assert np.isclose(np.vdot(y, y).real, _fr(case["ynorm_sq"]))
+    res = pursuits.cosamp(Phi, y, case["K"])
+    assert len(res["trace"]) == len(case["trace"])
+    for got, want in zip(res["trace"], case["trace"]):
+        assert got["T"].tolist() == want["T"] and got["S"].tolist() == want["S"]
+        assert np.allclose(got["b"], [_fr(v) for v in want["b"]], atol=1e-13)
+        assert np.allclose(got["x"], [_fr(v) for v in want["x"]], atol=1e-13)
+        assert np.isclose(got["rn"] ** 2, _fr(want["rn_sq"]), atol=1e-13)
+        assert got["accepted"] == want["accepted"]
+    assert res["support"].tolist() == case["support"] and res["iters"] == case["iters"]
+    assert np.allclose(res["x"], [_fr(v) for v in case["x"]], atol=1e-13)
+    assert np.allclose(np.square(res["resnorm"]), [_fr(case["ynorm_sq"])] +
+                       [_fr(t["rn_sq"]) for t in case["trace"] if t["accepted"]], atol=1e-13)
+
+
+# ------------------------------------------- what each step defines
+def _is_top(v, chosen, k, pool):
+    """`chosen` is the k largest |v| over `pool` with ties to the lower index:
+    every chosen j beats every pool member left out."""
+    pool = [int(j) for j in pool]
+    chosen = [int(j) for j in chosen]
+    if len(chosen) != min(k, len(pool)) or not set(chosen) <= set(pool):
+        return False
+    a = np.abs(v) ** 2
+    out = [j for j in pool if j not in chosen]
+    return all(a[i] > a[o] or (a[i] == a[o] and i < o) for i in chosen for o in out)
+
+
+def _ls_optimal(Phi, y, cols, x):
+    """x solves the least squares on cols: the residual is orthogonal to them."""
+    P = Phi[:, np.asarray(cols, dtype=np.int64)]
+    return np.max(np.abs(P.conj().T @ (y - P @ x))) <= 1e-10 * np.linalg.norm(y)
+
+
+def _noisy(kind, N, M, K, snr, seed):
+    rng = np.random.default_rng(seed)
+    om = synth.draw_omega(N, M, rng)
+    Phi = matrices.sensing(kind, N, om)
+    y = synth.add_noise(synth.measure(kind, N, om, synth.draw_support(N, K, rng),
+                                      synth.draw_values(K, kind, "gauss", rng)), snr, rng)
+    return Phi, y
+
+
+# seeds 724 (WHT) and 735 (DFT) end on a rejected iterate whose support
+# differs from the accepted one
+SP_SEEDS = [700, 701, 702, 724, 735]
+COSAMP_SEEDS = [800, 801, 802, 700, 811]  # 700 (WHT), 811 (DFT): the same for CoSaMP
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("seed", SP_SEEDS)
+def test_sp_steps_follow_their_definitions(kind, seed):
+    N, M, K = 128, 48, 6
+    Phi, y = _noisy(kind, N, M, K, 12.0, seed)
+    res = pursuits.subspace_pursuit(Phi, y, K)
+    T, x, rn = res["T0"], res["x0"], res["resnorm"][0]
+    assert _is_top(Phi.conj().T @ y, T, K, range(N)) and _ls_optimal(Phi, y, T, x)
+    accepted = [rn]
+    for st in res["trace"]:
+        h = Phi.conj().T @ (y - Phi[:, T] @ x)
+        new = sorted(set(st["Tp"].tolist()) - set(T.tolist()))
+        assert set(T.tolist()) <= set(st["Tp"].tolist()) and len(st["Tp"]) == 2 * K
+        assert _is_top(h, new, K, [j for j in range(N) if j not in set(T.tolist())])
+        assert _ls_optimal(Phi, y, st["Tp"], st["b"])
+        assert _is_top(st["b"], [i for i, j in enumerate(st["Tp"]) if j in set(st["Tn"].tolist())], K,
+                       range(len(st["Tp"])))
+        assert _ls_optimal(Phi, y, st["Tn"], st["x"])
+        assert np.isclose(st["rn"], np.linalg.norm(y - Phi[:, st["Tn"]] @ st["x"]))
+        assert st["accepted"] == (st["rn"] < rn)
+        if not st["accepted"]:
+            break
+        T, x, rn = st["Tn"], st["x"], st["rn"]
+        accepted.append(rn)
+    assert res["support"].tolist() == T.tolist() and np.array_equal(res["x"], x)
+    assert np.allclose(res["resnorm"], accepted)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("seed", COSAMP_SEEDS)
+def test_cosamp_steps_follow_their_definitions(kind, seed):
+    N, M, K = 128, 56, 5
+    Phi, y = _noisy(kind, N, M, K, 12.0, seed)
+    res = pursuits.cosamp(Phi, y, K)
+    S, x, rn = np.zeros(0, np.int64), np.zeros(0, complex), np.linalg.norm(y)
+    for st in res["trace"]:
+        h = Phi.conj().T @ (y - (Phi[:, S] @ x if len(S) else 0))
+        extra = sorted(set(st["T"].tolist()) - set(S.tolist()))
+        top = pursuits.top_k(h, 2 * K)
+        assert set(st["T"].tolist()) == set(top.tolist()) | set(S.tolist())
+        assert _is_top(h, top, 2 * K, range(N)) and set(extra) <= set(top.tolist())
+        assert _ls_optimal(Phi, y, st["T"], st["b"])
+        keep = [i for i, j in enumerate(st["T"]) if j in set(st["S"].tolist())]
+        assert _is_top(st["b"], keep, K, range(len(st["T"])))
+        assert np.array_equal(st["x"], st["b"][keep])  # pruned, not solved again
+        assert np.isclose(st["rn"], np.linalg.norm(y - Phi[:, st["S"]] @ st["x"]))
+        assert st["accepted"] == (st["rn"] < rn)
+        if not st["accepted"]:
+            break
+        S, x, rn = st["S"], st["x"], st["rn"]
+    assert res["support"].tolist() == S.tolist() and np.array_equal(res["x"], x)
