@@ -91,10 +91,11 @@ def columns(kind: str, N: int, omega, support) -> np.ndarray:
     return np.exp(-2j * np.pi * ((om * k) % N) / N) / np.sqrt(N)
 
 
-def omp(kind: str, N: int, omega, y, K: int, rel_tol: float = 1e-6, dep_tol: float = DEP_TOL) -> dict:
+def omp(kind: str, N: int, omega, y, K: int, rel_tol: float = 1e-6, dep_tol: float = DEP_TOL,
+        record_x: bool = False) -> dict:
     """Algorithm 1.1 with transform-based steps 2 and 7; same outputs as
     oracle.omp.omp (support in selection order, x, iters, resnorm history,
-    gaps, d2, halt)."""
+    gaps, d2, halt); with ``record_x`` also every iterate x_t ("xs")."""
     omega = np.asarray(omega, dtype=np.int64)
     M = len(omega)
     cplx = kind == "dft" or np.iscomplexobj(y)
@@ -127,6 +128,8 @@ def omp(kind: str, N: int, omega, y, K: int, rel_tol: float = 1e-6, dep_tol: flo
         out["gap"].append(gap)
         out["d2"].append(d2)
         x, _ = least_squares(Phi_t, y)             # step 6
+        if record_x:
+            out.setdefault("xs", []).append(x)
         r = y - synthesize(kind, N, omega, lam, x)  # step 7
         rn = float(np.linalg.norm(r))
         out["resnorm"].append(rn)

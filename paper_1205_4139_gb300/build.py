@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libcsfast.so")
 UNITS = ["cs_api.cu", "cs_kernels.cu", "cs_omp.cu", "cs_pursuit.cu", "cs_noalloc.cu", "cs_large.cu", "cs_serve.cu",
-         "cs_omp_cluster.cu", "cs_omp_multi.cu"]
+         "cs_omp_cluster.cu", "cs_omp_multi.cu", "cs_wht_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -55,6 +55,7 @@ enum { CFMT_FULL = 0, CFMT_HALF = 1, CFMT_INT = 2 };
 
 // Bits of the device status word.
 constexpr int kStatusPhaseBound = 1;  // the OMP kernel's phase loop hit its bound
+constexpr int kStatusTcTimeout = 2;   // a tensor-core transform's MMAs did not complete in time
 
 struct OmpLaunch {
   const void* y;
@@ -98,6 +99,11 @@ cudaError_t launch_expand_c(const PlanView& P, void* out, bool fp32, cudaStream_
 cudaError_t launch_kernel_vector(const PlanView& P, void* c64_full, cudaStream_t st);
 
 // transforms / correlations
+// Conventional correlation of partial-WHT FP32 plans (16 <= N <= 8192) with
+// the radix-16 Hadamard stages on the tensor cores (cs_wht_tc.cu).
+bool wht_tc_applies(const PlanView& P);
+cudaError_t launch_correlate_wht_tc(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax,
+                                    cudaStream_t st);
 cudaError_t launch_correlate(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax,
                              cudaStream_t st);
 cudaError_t launch_correlate_fast(const PlanView& P, const void* h0, const int32_t* supp, const void* x,

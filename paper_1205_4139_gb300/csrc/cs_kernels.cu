@@ -162,6 +162,7 @@ static cudaError_t corr_impl(const PlanView& P, const void* r, int64_t batch, vo
 cudaError_t launch_correlate(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax,
                              cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
+  if (wht_tc_applies(P)) return launch_correlate_wht_tc(P, r, batch, h, amax, st);
   if (P.dft) return P.fp32 ? corr_impl<float2>(P, r, batch, h, amax, st) : corr_impl<double2>(P, r, batch, h, amax, st);
   return P.fp32 ? corr_impl<float>(P, r, batch, h, amax, st) : corr_impl<double>(P, r, batch, h, amax, st);
 }
