@@ -332,9 +332,46 @@ def secondary(args, dev, plan, inst, stream, flush, refs=None):
     out["cosamp_M64_N8192_K4"] = {"ms_per_instance_iteration": per_it,
                                   "fast_over_conv": per_it["fast"] / per_it["conv"],
                                   "paper_flop_model": costmodel.cosamp_fast_ratio(8192, 4)}
+    out["wht_fp32_correlate"] = {"N4096": wht_correlate(dev, stream),
+                                 "N256": wht_correlate(dev, stream, N=256, M=64, B=1 << 20, tc_default=True)}
     out["large_dft_c64_N4194304_M524288"] = large_single(dev, stream, flush)
     out["serving"] = serving(args.serve_requests)
     out["uneven_batch"] = uneven(args.uneven_instances, refs.get("uneven") if refs else None)
+    return out
+
+
+def wht_correlate(dev, stream, N=4096, M=1024, B=65536, tc_default=False):
+    """Batched conventional correlation h = Phi^H r of a partial-WHT FP32 plan
+    (cs_correlate), with the radix-16 Hadamard stages as butterflies on the
+    CUDA cores (default) and on the tensor cores (CS_PLAN_TENSOR_CORES):
+    B residuals of M entries -> B correlations of N entries (inputs and
+    outputs about 1.3 GB, beyond L2).  Against HBM: algorithmic bytes per
+    correlation = M * 4 (r) + N * 4 (h); the slot map (N * 4) is shared by the
+    batch and stays in L2."""
+    import torch
+    from paper_1205_4139_gb300 import binding
+    import ctypes
+    rng = np.random.default_rng(9)
+    om = synth.draw_omega(N, M, rng)
+    r = torch.randn(B, M, dtype=torch.float32, device=dev)
+    h = torch.empty(B, N, dtype=torch.float32, device=dev)
+    am = torch.empty(B, dtype=torch.int32, device=dev)
+    L = binding.load()
+    st = ctypes.c_void_p(stream.cuda_stream)
+    byts = B * (M * 4 + N * 4)
+    hbm = json.load(open(PEAKS_FILE))["hbm_gbs"] if os.path.exists(PEAKS_FILE) else 6800.0
+    out = {"workload": f"partial WHT FP32, N={N}, M={M}, {B} residuals, cs_correlate", "bytes": byts}
+    names = (("tensor_core_radix16", False), ("tensor_core_radix16_flag", True)) if tc_default else \
+        (("cuda_core_butterflies", False), ("tensor_core_radix16", True))
+    for name, tc in names:
+        plan = binding.Plan(N, om, "wht", "fp32", tensor_cores=tc)
+
+        def call():
+            binding._check(L.cs_correlate(plan._h, ctypes.c_void_p(r.data_ptr()), B, ctypes.c_void_p(h.data_ptr()),
+                                          ctypes.c_void_p(am.data_ptr()), st))
+        ms = statistics.median(_events_ms(call, 10, 3, stream))
+        out[name] = {"ms": ms, "correlations_per_s": B / ms * 1e3, "gbs": byts / ms / 1e6,
+                     "frac_of_hbm": byts / ms / 1e6 / hbm, "device_error": plan.device_error()}
     return out
 
 
@@ -698,6 +735,18 @@ def run_gpu(args, rank: int, world: int, refs=None):
     total_ms, e2e_mean, fast_med, conv_med = replicas.max_over_ranks(
         [total_ms, sum(e2e_ms) / len(e2e_ms), statistics.median(fast_ms), statistics.median(conv_ms)], dev)
 
+    # FP32 FMA-pipe peak measured in this run (cs_fma_probe), beside the
+    # figure derived from unit counts and the maximum clock
+    probe = []
+    for _ in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = binding.fma_probe(1 << 14, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        probe.append(fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    fp32_measured = max(probe[1:])
+
     flops = correlation_flops(N, it_np, best_ts, "hybrid")
     per_launch_ms = total_ms / args.steps
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
@@ -713,8 +762,10 @@ def run_gpu(args, rank: int, world: int, refs=None):
         "conv": {"solves_per_s": B * world / (conv_med * 1e-3), "ms_per_step_p50": conv_med},
         "e2e": {"value": B * world / (e2e_mean * 1e-3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_measured, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_measured, "traffic": None,
+                     "peak_source": "FP32 FMA pipe measured in this run (cs_fma_probe, best of 5)",
+                     "peak_derived": FP32_PEAK_TFLOPS, "frac_of_derived": achieved / FP32_PEAK_TFLOPS},
         "clocks": clk.summary(),
         "gpu_launches": args.steps,
         "iters_mean": float(it_np.mean()),

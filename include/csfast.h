@@ -106,11 +106,26 @@ cs_status cs_plan_create(int64_t N, const int32_t* omega_host, int64_t M, int32_
  *   CS_PLAN_C_INT   WHT: N c(d) = M - 2 #{i in Omega : popcount(i & d) odd}
  *                   is an integer, stored exactly as int32 (half the memory
  *                   of an FP64 c, no FP copy) */
-enum { CS_PLAN_C_HALF = 1u, CS_PLAN_C_INT = 2u };
+enum { CS_PLAN_C_HALF = 1u, CS_PLAN_C_INT = 2u, CS_PLAN_TENSOR_CORES = 4u };
+
+/* Tensor-core Hadamard transform (WHT FP32 plans).  cs_correlate computes
+ * the fast Hadamard transform of Sec. III-B (Table I, 2N log2 N) with its
+ * radix-16 stages on the tensor cores: each 16-point group is multiplied by
+ * the +-1 matrix H_16 (tcgen05 MMAs, the FP32 data split exactly into three
+ * BF16 parts, FP32 accumulation in tensor memory), the remaining radix-2, -4
+ * or -8 stage on the CUDA cores; results agree with the FP32 transform to
+ * FP32 accumulation error (bit-exact on a single nonzero).  This is the
+ * default for 16 <= N <= 512, where it is faster on GB300 than the CUDA-core
+ * butterflies; CS_PLAN_TENSOR_CORES extends it to N <= 4096, where the
+ * butterflies are faster (the transform moves more bytes than it does
+ * arithmetic, and splitting the operands costs more instructions than the
+ * butterflies it replaces).  A device-detected timeout of the tensor-core
+ * pipeline sets bit 1 of the plan's status word. */
 
 /* cs_plan_create with storage flags (0 = full vector, as cs_plan_create).
  * CS_ERR_INVALID for unknown flags, CS_PLAN_C_HALF on a WHT plan,
- * CS_PLAN_C_INT on a DFT plan, or both. */
+ * CS_PLAN_C_INT on a DFT plan, both, or CS_PLAN_TENSOR_CORES on anything but
+ * a WHT FP32 plan. */
 cs_status cs_plan_create_ex(int64_t N, const int32_t* omega_host, int64_t M, int32_t kind, int32_t prec,
                             uint32_t flags, void* stream, cs_plan_t* out);
 
@@ -137,7 +152,9 @@ cs_status cs_plan_switch(cs_plan_t plan, int32_t* t_switch);
 
 /* Errors the kernels detected on the device since the last call (0 = none;
  * bit 0: an OMP launch stopped because its phase loop reached its bound,
- * which leaves that launch's outputs incomplete).  Synchronises `stream`,
+ * which leaves that launch's outputs incomplete; bit 1: a tensor-core
+ * transform's MMAs did not complete within its wait bound, which leaves that
+ * call's outputs incomplete).  Synchronises `stream`,
  * then clears the word. */
 cs_status cs_plan_status(cs_plan_t plan, int32_t* device_error, void* stream);
 
@@ -370,6 +387,15 @@ cs_status cs_server_destroy(cs_server_t server);
  * budget in use and the budget, the index of the job to start now, or -1. */
 int32_t cs_admit_next(const int64_t* footprints, const int32_t* bypassed, int32_t n_pending, int64_t in_use,
                       int64_t budget, int32_t max_bypass);
+
+/* Measurement helper (the paper has no counterpart): queues on `stream` a
+ * kernel of independent FP32 fused multiply-adds over the whole GPU, iters
+ * steps of eight chains per thread, and writes its flop count to *flops
+ * (host).  Timing it with events on `stream` gives the FP32 non-tensor peak
+ * that the kernel-sum correlation's roofline fraction is stated against.
+ * sink_dev may be NULL (nothing is written).  CS_ERR_INVALID for iters < 1 or
+ * flops NULL. */
+cs_status cs_fma_probe(int32_t iters, float* sink_dev, double* flops, void* stream);
 
 /* Short static description of a status code. */
 const char* cs_status_string(cs_status s);

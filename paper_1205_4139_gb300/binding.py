@@ -25,7 +25,7 @@ PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 EXPORTS = ["cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_switch", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
            "cs_correlate_fast", "cs_omp", "cs_omp_batched", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
            "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy",
-           "cs_admit_next", "cs_status_string", "cs_last_error"]
+           "cs_admit_next", "cs_fma_probe", "cs_status_string", "cs_last_error"]
 
 
 class CsError(RuntimeError):
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
     L.cs_server_destroy.argtypes = [vp]
     L.cs_admit_next.argtypes = [pi64, pi32, i32, i64, i64, i32]
     L.cs_admit_next.restype = ctypes.c_int32
+    L.cs_fma_probe.argtypes = [i32, vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.cs_fma_probe.restype = ctypes.c_int
     for f in ("cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_switch", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
               "cs_correlate_fast", "cs_omp", "cs_omp_batched", "cs_sp", "cs_cosamp", "cs_omp_noalloc",
               "cs_plan_tune", "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy"):
@@ -135,12 +137,14 @@ def ls_dtype(kind: str):
 class Plan:
     """A plan for Phi = S_Omega A (cs_plan_create)."""
 
-    def __init__(self, N: int, omega, kind: str = "dft", prec: str = "fp32", stream=None, c_storage: str = "full"):
-        """c_storage: 'full', 'half' (DFT, CS_PLAN_C_HALF) or 'int' (WHT, CS_PLAN_C_INT)."""
+    def __init__(self, N: int, omega, kind: str = "dft", prec: str = "fp32", stream=None, c_storage: str = "full",
+                 tensor_cores: bool = False):
+        """c_storage: 'full', 'half' (DFT, CS_PLAN_C_HALF) or 'int' (WHT, CS_PLAN_C_INT);
+        tensor_cores: CS_PLAN_TENSOR_CORES (WHT FP32)."""
         L = load()
         om = np.ascontiguousarray(np.asarray(omega, dtype=np.int32))
         self.N, self.M, self.kind, self.prec = int(N), int(om.size), kind, prec
-        flags = {"full": 0, "half": 1, "int": 2}[c_storage]
+        flags = {"full": 0, "half": 1, "int": 2}[c_storage] | (4 if tensor_cores else 0)
         h = ctypes.c_void_p()
         _check(L.cs_plan_create_ex(self.N, om.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.M, KINDS[kind],
                                    PRECS[prec], flags, _stream(stream), ctypes.byref(h)))
@@ -381,3 +385,10 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def fma_probe(iters: int = 1 << 14, stream=None) -> float:
+    """cs_fma_probe: queue the FP32 FMA probe on the stream; returns its flops."""
+    f = ctypes.c_double()
+    _check(load().cs_fma_probe(int(iters), None, ctypes.byref(f), _stream(stream)))
+    return f.value

@@ -171,7 +171,8 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
                                   uint32_t flags, void* stream, bool ordered, cs_plan_t* out) {
   if (!out) return CS_ERR_INVALID;
   *out = nullptr;
-  if (flags & ~(uint32_t)(CS_PLAN_C_HALF | CS_PLAN_C_INT)) return CS_ERR_INVALID;
+  if (flags & ~(uint32_t)(CS_PLAN_C_HALF | CS_PLAN_C_INT | CS_PLAN_TENSOR_CORES)) return CS_ERR_INVALID;
+  if ((flags & CS_PLAN_TENSOR_CORES) && (kind != CS_WHT || prec != CS_FP32)) return CS_ERR_INVALID;
   if ((flags & CS_PLAN_C_HALF) && kind != CS_DFT) return CS_ERR_INVALID;
   if ((flags & CS_PLAN_C_INT) && kind != CS_WHT) return CS_ERR_INVALID;
   if (kind != CS_WHT && kind != CS_DFT) return CS_ERR_INVALID;
@@ -206,6 +207,7 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
   p->v.n2 = large ? logN - logN / 2 : 0;
   p->v.wsh = large ? (logN + 1) / 2 : 0;
   p->v.cfmt = (flags & CS_PLAN_C_HALF) ? CFMT_HALF : ((flags & CS_PLAN_C_INT) ? CFMT_INT : CFMT_FULL);
+  p->v.tc = (flags & CS_PLAN_TENSOR_CORES) != 0;
   // Sec. IV excessive point under the Table I flop model
   p->t_switch_default = kind == CS_DFT ? 1 + (5 * logN) / 6 : 1 + logN;
 
@@ -835,5 +837,14 @@ extern "C" cs_status cs_plan_tune(cs_plan_t plan, const void* y_dev, int64_t bat
 extern "C" cs_status cs_plan_switch(cs_plan_t plan, int32_t* t_switch) {
   if (!plan || !t_switch) return CS_ERR_INVALID;
   *t_switch = plan_switch(plan);
+  return CS_OK;
+}
+
+extern "C" cs_status cs_fma_probe(int32_t iters, float* sink_dev, double* flops, void* stream) {
+  using namespace csf;
+  if (iters < 1 || !flops) return CS_ERR_INVALID;
+  double f = 0.0;
+  CS_CUDA(launch_fma_probe(iters, sink_dev, (cudaStream_t)stream, &f), "fma probe");
+  *flops = f;
   return CS_OK;
 }

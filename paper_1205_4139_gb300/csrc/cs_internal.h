@@ -37,6 +37,9 @@ struct PlanView {
   // integers N c(d) and c64 / c32 are unused
   int cfmt;
   const int* ci;
+  // WHT FP32, 16 <= N <= 4096: cs_correlate runs the radix-16 Hadamard
+  // stages on the tensor cores (CS_PLAN_TENSOR_CORES)
+  bool tc;
   // the one-CTA radix-16 chains (N <= 2^16): slot map in the chains' position
   // order and, for DFT, the chains' twiddles (FP64 / FP32).  For N <= 8192
   // these are slot / tw64 / tw32; for 8192 < N <= 2^16 the slot map is the
@@ -99,8 +102,11 @@ cudaError_t launch_expand_c(const PlanView& P, void* out, bool fp32, cudaStream_
 cudaError_t launch_kernel_vector(const PlanView& P, void* c64_full, cudaStream_t st);
 
 // transforms / correlations
-// Conventional correlation of partial-WHT FP32 plans (16 <= N <= 8192) with
-// the radix-16 Hadamard stages on the tensor cores (cs_wht_tc.cu).
+// FP32 FMA-pipe probe (cs_fma_probe): queues the kernel, returns its flop count.
+cudaError_t launch_fma_probe(int iters, float* sink, cudaStream_t st, double* flops);
+// Conventional correlation of partial-WHT FP32 plans (16 <= N <= 4096) with
+// the radix-16 Hadamard stages on the tensor cores (cs_wht_tc.cu), for plans
+// created with CS_PLAN_TENSOR_CORES.
 bool wht_tc_applies(const PlanView& P);
 cudaError_t launch_correlate_wht_tc(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax,
                                     cudaStream_t st);

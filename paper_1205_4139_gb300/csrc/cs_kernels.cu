@@ -234,4 +234,34 @@ cudaError_t launch_correlate_fast(const PlanView& P, const void* h0, const int32
                 : fast_impl<double>(P, h0, supp, x, s, batch, h, amax, st);
 }
 
+// ---------------------------------------------------- FP32 FMA-pipe probe
+// Eight independent FMA chains per thread, `iters` steps each: the FP32
+// non-tensor peak the kernel-sum correlation is measured against.  The
+// result is only stored when it equals an impossible value, so the chains
+// are not removed and nothing is written.
+__global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, float* sink) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1e-3f * (float)(threadIdx.x + k);
+  const float m = 0.999999f, c = 1e-7f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], m, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == -12345.f && sink) sink[0] = s;
+}
+
+cudaError_t launch_fma_probe(int iters, float* sink, cudaStream_t st, double* flops) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = sms * 8;
+  *flops = 2.0 * 8.0 * (double)iters * (double)kThreads * (double)grid;
+  fma_probe_kernel<<<grid, kThreads, 0, st>>>(iters, sink);
+  return cudaGetLastError();
+}
+
 }  // namespace csf

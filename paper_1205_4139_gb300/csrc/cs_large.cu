@@ -1621,9 +1621,22 @@ __global__ void __launch_bounds__(kLT) lp_step_kernel(LPArgs<E> a, int phase) {
       for (int i = threadIdx.x; i < kp; i += kLT) lv.g[i] = lv.x[sel2[i]];
     g.sync();
     if (a.algo == 0) {
-      ls_set(T, kp);                        // x_new = LS on T_new
-      if (threadIdx.x == 0) X.rn2_new = X.ls_rn2;
+      // T_new equal to the accepted support (both ascending): the solve would
+      // repeat the accepted one, so the iteration is rejected without it
+      if (threadIdx.x == 0) {
+        bool same = kp == X.ns;
+        for (int i = 0; same && i < kp; ++i) same = T[i] == S[i];
+        scr[0] = same;
+      }
       g.sync();
+      if (scr[0]) {
+        if (threadIdx.x == 0) X.rn2_new = X.rn2;
+        g.sync();
+      } else {
+        ls_set(T, kp);                        // x_new = LS on T_new
+        if (threadIdx.x == 0) X.rn2_new = X.ls_rn2;
+        g.sync();
+      }
     } else {
       // ||y - Phi x||^2 = ||y||^2 - 2 Re x^H h_0(S) + x^H G_S x  (FP64)
       double acc[2] = {0.0, 0.0};

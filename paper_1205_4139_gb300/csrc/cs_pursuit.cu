@@ -246,9 +246,23 @@ __global__ void __launch_bounds__(kPThreads) pursuit_kernel(PursuitArgs<E> a) {
         }
         g.sync();
         if (a.algo == ALGO_SP) {
-          ls_set(g, a.P, lv, h0, T, kk, st, sh);        // x_new = LS on T_new
-          if (g.tid == 0) st.rn2_new = st.ls_rn2;
+          // T_new equal to the accepted support (both ascending): x_new and
+          // its residual are the accepted ones (the same solve in the same
+          // column order), so the iteration is rejected without solving
+          if (g.tid == 0) {
+            bool same = kk == st.ns;
+            for (int i = 0; same && i < kk; ++i) same = T[i] == S[i];
+            scr[0] = same;
+          }
           g.sync();
+          if (scr[0]) {
+            if (g.tid == 0) st.rn2_new = st.rn2;
+            g.sync();
+          } else {
+            ls_set(g, a.P, lv, h0, T, kk, st, sh);        // x_new = LS on T_new
+            if (g.tid == 0) st.rn2_new = st.ls_rn2;
+            g.sync();
+          }
         } else {
           // ||y - Phi x||^2 = ||y||^2 - 2 Re x^H h_0(S) + x^H G_S x  (FP64)
           double acc[2] = {0.0, 0.0};

@@ -17,8 +17,9 @@
 //              += H x_lo), so the only rounding is the FP32 accumulation.
 //
 // One CTA of 128 threads (one warpgroup: thread t reads TMEM lane t, i.e.
-// row t of every D tile) transforms V vectors at a time (V N = 8192 elements,
-// up to 4 tiles of 128 groups per stage).  Per stage: the threads write the
+// row t of every D tile) transforms V vectors at a time (V N = 4096 elements,
+// up to 2 tiles of 128 groups per stage; about 41 KB of shared memory, so
+// five CTAs share an SM).  Per stage: the threads write the
 // split A tiles, one thread issues 3 MMAs per tile and commits them to an
 // mbarrier, the threads wait on it (bounded), read D with tcgen05.ld and
 // write the results back.  A last radix-2^r stage (r = log2 N mod 4) runs on
@@ -33,8 +34,8 @@ namespace csf {
 namespace {
 
 constexpr int kTT = 128;            // threads per CTA: one warpgroup
-constexpr int kElems = 8192;        // elements (V vectors x N) per CTA round
-constexpr int kMaxTiles = kElems / 16 / 128;  // 128-row tiles per stage: 4
+constexpr int kElems = 4096;        // elements (V vectors x N) per CTA round
+constexpr int kMaxTiles = kElems / 16 / 128;  // 128-row tiles per stage: 2
 constexpr int kTileBytes = 4096;    // 128 rows x 16 BF16
 constexpr int kTmemCols = 16 * kMaxTiles;     // one 16-column FP32 accumulator per tile
 constexpr long long kSpinLimit = 1LL << 22;   // bound on the mbarrier wait (about a second)
@@ -328,7 +329,15 @@ __global__ void __launch_bounds__(kTT) wht_tc_kernel(PlanDev<float> P, const flo
 
 }  // namespace
 
-bool wht_tc_applies(const PlanView& P) { return !P.dft && P.fp32 && !P.large && P.logN >= 4 && P.logN <= kMaxLogN; }
+// WHT FP32 plans take the tensor-core transform for 16 <= N <= 512 by
+// default (measured on GB300: 2.3x the CUDA-core butterflies' throughput at
+// N = 256, where one 256-thread CTA per vector leaves the butterfly kernel
+// latency-bound), and up to N = 4096 when the plan asks for it
+// (CS_PLAN_TENSOR_CORES; slower than the butterflies from N = 1024 on).
+bool wht_tc_applies(const PlanView& P) {
+  if (P.dft || !P.fp32 || P.large || P.logN < 4) return false;
+  return P.logN <= (P.tc ? 12 : 9);
+}
 
 cudaError_t launch_correlate_wht_tc(const PlanView& P, const void* r, int64_t batch, void* h, int32_t* amax,
                                     cudaStream_t st) {
@@ -336,15 +345,21 @@ cudaError_t launch_correlate_wht_tc(const PlanView& P, const void* r, int64_t ba
   const size_t smem = tc_layout().total;
   cudaError_t e = raise_smem_limit((const void*)wht_tc_kernel, smem);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, occ = 0;
+  // as much of the unified L1 / shared memory as possible goes to shared
+  // memory, so that several CTAs share an SM and hide each other's latency
+  e = cudaFuncSetAttribute(wht_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, smem_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wht_tc_kernel, kTT, smem);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) return cudaErrorInvalidConfiguration;
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  // CTAs per SM by shared memory (each also holds kTmemCols of the 512
+  // tensor-memory columns, which allows up to 16)
+  int per_sm = smem_sm / (int)(smem + 2048);
+  per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
   const int64_t vmax = kElems >> P.logN;
   const int64_t rounds = (batch + vmax - 1) / vmax;
-  const int64_t cap = (int64_t)occ * sms;
+  const int64_t cap = (int64_t)per_sm * sms;
   const int grid = (int)(rounds < cap ? rounds : cap);
   wht_tc_kernel<<<grid, kTT, smem, st>>>(plan_dev<float>(P), (const float*)r, batch, (float*)h, amax, P.status);
   return cudaGetLastError();

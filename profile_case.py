@@ -10,6 +10,11 @@ cs_omp_batched calls (the second is the one to capture).
   python profile_case.py [batch]
   python profile_case.py 1 single
   python profile_case.py uneven dft big 304
+  python profile_case.py wht_tc 16384 4096
+
+With `wht_tc`, two cs_correlate calls on `batch` residuals of a partial-WHT
+FP32 plan with N points and M = N/4 rows (the tensor-core Hadamard stages;
+the second call is the one to capture).
 """
 import os
 import sys
@@ -50,6 +55,17 @@ def main():
 
     if len(sys.argv) > 1 and sys.argv[1] == "uneven":
         uneven(sys.argv[2], sys.argv[3], int(sys.argv[4]))
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "wht_tc":
+        import numpy as np
+        B, N = int(sys.argv[2]), int(sys.argv[3])
+        plan = binding.Plan(N, synth.draw_omega(N, N // 4, np.random.default_rng(1)), "wht", "fp32", tensor_cores=True)
+        r = torch.randn(B, N // 4, device="cuda")
+        for _ in range(2):
+            plan.correlate(r)
+        torch.cuda.synchronize()
+        assert plan.device_error() == 0
+        print("ok")
         return
     B = int(sys.argv[1]) if len(sys.argv) > 1 else 456
     single = len(sys.argv) > 2 and sys.argv[2] == "single"

@@ -1,12 +1,13 @@
 """The conventional correlation of partial-WHT FP32 plans on the tensor
-cores (cs_correlate: h = A^H zf_Omega(r), Algorithm 1.1 step 2, the FHT of
-Sec. III-B) against the FP64 oracle.
+cores (plans created with CS_PLAN_TENSOR_CORES; cs_correlate:
+h = A^H zf_Omega(r), Algorithm 1.1 step 2, the FHT of Sec. III-B) against the
+FP64 oracle.
 
 The radix-16 Hadamard stages run as tcgen05 MMAs on three BF16 parts of the
 FP32 data (exact: +-1 times an exactly split value), accumulated in FP32, so
 h carries FP32 accumulation error only: far inside the 2e-5 FP32 tolerance
-(the tests ask for 1e-6).  Sizes cover one vector per CTA round (N = 8192),
-many vectors per round (N = 16 .. 4096), a ragged last round, the remainder
+(the tests ask for 1e-6).  Sizes cover one vector per CTA round (N = 4096),
+many vectors per round (N = 16 .. 2048), the CUDA-core path above 4096, a ragged last round, the remainder
 stage (log2 N mod 4 = 1, 2, 3), values over 12 orders of magnitude (the split
 must keep every bit), exact ties of |h| (lowest j wins) and the status word.
 """
@@ -35,7 +36,7 @@ def rel_inf(a, b):
 def test_tc_correlate_matches_oracle(N, M, B):
     rng = np.random.default_rng(N + B)
     om = synth.draw_omega(N, M, rng)
-    plan = binding.Plan(N, om, "wht", "fp32")
+    plan = binding.Plan(N, om, "wht", "fp32", tensor_cores=True)
     r = rng.standard_normal((B, M)).astype(np.float32)
     h, am = plan.correlate(torch.from_numpy(r).cuda())
     h, am = h.cpu().numpy(), am.cpu().numpy()
@@ -64,7 +65,7 @@ def test_tc_split_keeps_every_bit(N):
     assert np.array_equal(x.astype(np.float64), mant * np.abs(x) / mant * np.sign(x))  # exact in FP32
     r = np.zeros((B, N), np.float32)
     r[np.arange(B), pos] = x
-    plan = binding.Plan(N, np.arange(N, dtype=np.int32), "wht", "fp32")
+    plan = binding.Plan(N, np.arange(N, dtype=np.int32), "wht", "fp32", tensor_cores=True)
     h, _ = plan.correlate(torch.from_numpy(r).cuda())
     h = h.cpu().numpy()
     j = np.arange(N)
@@ -78,7 +79,7 @@ def test_tc_exact_ties_go_to_lowest_index():
     """Full sampling, r = two equal spikes: |h| is constant over j, every j
     ties, and the arg-max is j = 0."""
     N = 256
-    plan = binding.Plan(N, np.arange(N, dtype=np.int32), "wht", "fp32")
+    plan = binding.Plan(N, np.arange(N, dtype=np.int32), "wht", "fp32", tensor_cores=True)
     r = np.zeros((3, N), np.float32)
     r[:, 5] = 1.0
     r[1, 9] = 2.0  # |h| takes two values; ties among the larger ones
@@ -92,10 +93,26 @@ def test_tc_exact_ties_go_to_lowest_index():
 def test_tc_argmax_only_and_empty_batch():
     N, M = 1024, 300
     om = synth.draw_omega(N, M, np.random.default_rng(3))
-    plan = binding.Plan(N, om, "wht", "fp32")
+    plan = binding.Plan(N, om, "wht", "fp32", tensor_cores=True)
     r = torch.from_numpy(np.random.default_rng(4).standard_normal((40, M)).astype(np.float32)).cuda()
     h, am = plan.correlate(r)
     _, am2 = plan.correlate(r, want_h=False)
     assert torch.equal(am, am2)
     plan.correlate(torch.zeros(0, M, dtype=torch.float32, device="cuda"))
     assert plan.device_error() == 0
+
+
+def test_tc_flag_only_on_wht_fp32():
+    for kind, prec in (("dft", "fp32"), ("wht", "fp64")):
+        with pytest.raises(binding.CsError):
+            binding.Plan(64, np.arange(8, dtype=np.int32), kind, prec, tensor_cores=True)
+
+
+def test_tc_equals_cuda_core_path_to_rounding():
+    N, M, B = 4096, 1024, 64
+    om = synth.draw_omega(N, M, np.random.default_rng(5))
+    r = torch.from_numpy(np.random.default_rng(6).standard_normal((B, M)).astype(np.float32)).cuda()
+    ht, at = binding.Plan(N, om, "wht", "fp32", tensor_cores=True).correlate(r)
+    hc, ac = binding.Plan(N, om, "wht", "fp32").correlate(r)
+    ht, hc = ht.cpu().numpy(), hc.cpu().numpy()
+    assert np.max(np.abs(ht - hc)) <= 1e-6 * np.max(np.abs(hc))
