@@ -248,6 +248,34 @@ cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const void* cons
                          int32_t* const* supp_dev, int32_t* iters_dev, double* resnorm_dev,
                          void* stream);
 
+/* The autotuner of cs_omp_batched (the paper has no counterpart): measures,
+ * on the caller's uneven batch (same arguments as cs_omp_batched, hybrid
+ * path, outputs discarded), the launch shape of each launch group present,
+ * a group being the instances of one element type (kind, precision) and one
+ * residence (N <= 8192 in shared memory, 8192 < N <= 2^16 in global memory;
+ * instances with N > 2^16 are not tuned).  Per group it times the group's
+ * persistent launch alone (one warm-up, best of two) first with as many
+ * resident CTAs per SM as fit and with every smaller number (fewer CTAs keep
+ * fewer instance vectors in flight, which L2 may then hold), then at the
+ * best of those with the switch point of every instance at 16, 64 or 128
+ * (global memory; default 32) or 32 or 128 (shared memory; default the
+ * plan's), keeping a candidate only when it is 2 % faster.  The groups'
+ * launches share the GPU inside one cs_omp_batched call, so the per-group
+ * winners are then kept only if the whole call on the batch is 2 % faster
+ * with them (or with their switch points alone) than with the shapes stored
+ * before.  What is kept is stored per device and group for the process and
+ * used by later cs_omp_batched calls (CTAs per SM always; the switch point
+ * when their t_switch < 0).  If cap > 0, up to cap records (group = 4 DFT + 2 FP64 + 1
+ * global memory, CTAs per SM with 0 = all that fit, switch point with -1 =
+ * default, best time in ms) go to the output arrays (each NULL allowed) and
+ * their number to *n_out.  count = 0 forgets the shapes stored for the
+ * current device (later calls take the defaults again).  Allocates its
+ * temporary outputs on `stream` and blocks until done.  Errors as
+ * cs_omp_batched. */
+cs_status cs_omp_batched_tune(const cs_plan_t* plans, int64_t count, const void* const* y_dev, const int32_t* K,
+                              double rel_tol, int32_t* group_out, int32_t* ctas_out, int32_t* tswitch_out,
+                              float* ms_out, int32_t cap, int32_t* n_out, void* stream);
+
 /* Subspace pursuit and CoSaMP on `batch` measurements sharing the plan's
  * Omega, one CTA per instance for N <= 8192.  The paper applies its correlation to these
  * algorithms (Sec. I) and reports the cost of a fast CoSaMP (Sec. IV) without

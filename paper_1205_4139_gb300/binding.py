@@ -23,7 +23,7 @@ PRECS = {"fp64": CS_FP64, "fp32": CS_FP32}
 
 # Every function include/csfast.h declares.
 EXPORTS = ["cs_plan_create", "cs_plan_create_ex", "cs_plan_memory", "cs_plan_switch", "cs_plan_destroy", "cs_plan_info", "cs_plan_status", "cs_plan_kernel", "cs_correlate",
-           "cs_correlate_fast", "cs_omp", "cs_omp_batched", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
+           "cs_correlate_fast", "cs_omp", "cs_omp_batched", "cs_omp_batched_tune", "cs_sp", "cs_cosamp", "cs_omp_noalloc", "cs_plan_tune",
            "cs_server_create", "cs_server_submit", "cs_server_poll", "cs_server_stats", "cs_server_destroy",
            "cs_admit_next", "cs_fma_probe", "cs_status_string", "cs_last_error"]
 
@@ -81,6 +81,9 @@ def load(path: str = LIB_PATH):
     L.cs_omp_noalloc.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_omp_batched.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp), pi32, ctypes.POINTER(Halt),
                                  ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
+    L.cs_omp_batched_tune.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp), pi32, ctypes.c_double, pi32, pi32,
+                                      pi32, ctypes.POINTER(ctypes.c_float), i32, pi32, vp]
+    L.cs_omp_batched_tune.restype = ctypes.c_int
     L.cs_sp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_cosamp.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Halt), vp, vp, vp, vp, vp]
     L.cs_plan_tune.argtypes = [vp, vp, i64, i32, ctypes.c_double, pi32, pi32, ctypes.POINTER(ctypes.c_float), i32,
@@ -306,6 +309,29 @@ class Batch:
         _check(load().cs_omp_batched(self._plans, len(self.plans), self._y, self._K, ctypes.byref(hl), self._x,
                                      self._s, _ptr(self.iters), _ptr(self.resnorm), _stream(stream)))
         return self
+
+
+GROUPS = {0: "wht fp32 shared", 1: "wht fp32 global", 2: "wht fp64 shared", 3: "wht fp64 global",
+          4: "dft fp32 shared", 5: "dft fp32 global", 6: "dft fp64 shared", 7: "dft fp64 global"}
+
+
+def batch_tune(batch: "Batch", rel_tol: float = 1e-6, stream=None) -> list[dict]:
+    """cs_omp_batched_tune on a Batch's instances: the launch shape chosen for
+    each launch group, stored in the library for later cs_omp_batched calls."""
+    cap = 8
+    g, c, t = (ctypes.c_int32 * cap)(), (ctypes.c_int32 * cap)(), (ctypes.c_int32 * cap)()
+    ms, n = (ctypes.c_float * cap)(), ctypes.c_int32()
+    _check(load().cs_omp_batched_tune(batch._plans, len(batch.plans), batch._y, batch._K, rel_tol, g, c, t, ms, cap,
+                                      ctypes.byref(n), _stream(stream)))
+    return [{"group": GROUPS[g[i]], "ctas_per_sm": int(c[i]), "t_switch": int(t[i]), "ms": float(ms[i])}
+            for i in range(min(cap, n.value))]
+
+
+def batch_untune(stream=None):
+    """Forget the launch shapes batch_tune stored for the current device."""
+    n = ctypes.c_int32()
+    _check(load().cs_omp_batched_tune(None, 0, None, None, 1e-6, None, None, None, None, 0, ctypes.byref(n),
+                                      _stream(stream)))
 
 
 def omp_batched(plans, ys, Ks, rel_tol: float = 1e-6, path: str = "hybrid", t_switch: int = -1, stream=None):

@@ -137,6 +137,30 @@ namespace csf {
 int plan_switch_point(cs_plan_t plan) { return plan_switch(plan); }
 }  // namespace csf
 
+// Launch shapes of the uneven-batch launches that cs_omp_batched_tune
+// measured, per device and launch group (element type and residence):
+// resident CTAs per SM (0: as many as fit) and the switch point of calls with
+// t_switch < 0 (-1: the plan's, or 32 in global memory).
+namespace {
+struct BatchShape {
+  int ctas_per_sm = 0, t_switch = -1;
+};
+std::mutex g_shape_mu;
+std::map<std::pair<int, int>, BatchShape> g_shape;
+BatchShape batch_shape(int dev, int group) {
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  auto it = g_shape.find(std::make_pair(dev, group));
+  return it == g_shape.end() ? BatchShape{} : it->second;
+}
+void set_batch_shape(int dev, int group, BatchShape s) {
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  g_shape[std::make_pair(dev, group)] = s;
+}
+// launch group of a plan: DFT 4, FP64 2, global-memory residence 1
+size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+int batch_group(const csf::PlanView& v) { return (v.dft ? 4 : 0) + (v.fp32 ? 0 : 2) + (v.large ? 1 : 0); }
+}  // namespace
+
 static void plan_free(cs_plan_s* p) {
   if (!p) return;
   void* bufs[] = {p->d_slot, p->d_slot_chain, p->d_om_off, p->d_om_ent, p->d_tw64, p->d_tw32,
@@ -607,10 +631,13 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
     it.x = x_dev ? x_dev[b] : nullptr;
     it.supp = supp_dev[b];
     it.K = k;
-    it.t_switch = h.t_switch >= 0 ? h.t_switch : (p->v.large ? multi_switch_big(p->v.logN) : plan_switch(p));
+    const BatchShape shp = batch_shape(dev, batch_group(p->v));
+    it.t_switch = h.t_switch >= 0 ? h.t_switch
+                  : shp.t_switch >= 0 ? shp.t_switch
+                  : (p->v.large ? multi_switch_big(p->v.logN) : plan_switch(p));
     it.idx = (int)b;
     it.cost = multi_cost(p->v, k, it.t_switch, h.path);
-    group[(p->v.dft ? 4 : 0) + (p->v.fp32 ? 0 : 2) + (p->v.large ? 1 : 0)].push_back(it);
+    group[batch_group(p->v)].push_back(it);
   }
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -645,7 +672,8 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
   auto run = [&](const Job& j, cudaStream_t s) -> cs_status {
     if (j.group >= 0) {
       std::vector<MultiItem>& g = group[j.group];
-      const cudaError_t e = launch_omp_multi(g.data(), (int64_t)g.size(), h.rel_tol, h.path, iters_dev,
+      const cudaError_t e = launch_omp_multi(g.data(), (int64_t)g.size(), h.rel_tol, h.path,
+                                             batch_shape(dev, j.group).ctas_per_sm, iters_dev,
                                              resnorm_dev, plans[0]->v.status, s);
       return e == cudaSuccess ? CS_OK : cuda_fail(e, "omp_batched kernel");
     }
@@ -696,6 +724,187 @@ extern "C" cs_status cs_omp_batched(const cs_plan_t* plans, int64_t count, const
   cudaEventDestroy(fork);
   if (r != CS_OK) return r;
   CS_CUDA(e, "omp_batched streams");
+  return CS_OK;
+}
+
+// Measures the launch shapes of an uneven batch (the autotuner of
+// cs_omp_batched): for each launch group present (element type and
+// residence), the resident CTAs per SM and then the switch point, each
+// candidate timed on the group's own instances (one warm-up, best of two).
+extern "C" cs_status cs_omp_batched_tune(const cs_plan_t* plans, int64_t count, const void* const* y_dev,
+                                         const int32_t* K, double rel_tol, int32_t* group_out, int32_t* ctas_out,
+                                         int32_t* tswitch_out, float* ms_out, int32_t cap, int32_t* n_out,
+                                         void* stream) {
+  using namespace csf;
+  if (n_out) *n_out = 0;
+  if (count < 0 || !(rel_tol >= 0.0) || !std::isfinite(rel_tol) || cap < 0) return CS_ERR_INVALID;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (count == 0) {  // forget the shapes stored for this device
+    for (int gi = 0; gi < 8; ++gi) set_batch_shape(dev, gi, BatchShape{});
+    return CS_OK;
+  }
+  if (!plans || !y_dev || !K) return CS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<size_t> off((size_t)count, 0);
+  size_t tot = 0;
+  for (int64_t b = 0; b < count; ++b) {
+    const cs_plan_s* p = plans[b];
+    if (!p || p->device != dev) return CS_ERR_INVALID;
+    if (K[b] < 0 || K[b] > p->v.M || (p->v.M > 0 && !y_dev[b])) return CS_ERR_INVALID;
+    if (p->v.logN <= kMaxLogNMulti && (K[b] > kMaxK || (p->v.large && p->v.cfmt != CFMT_FULL)))
+      return CS_ERR_UNSUPPORTED;
+    if (p->v.logN > kMaxLogNMulti && K[b] > kMaxKLarge) return CS_ERR_UNSUPPORTED;
+    off[(size_t)b] = tot;
+    tot += a16((size_t)K[b] * 16) + a16((size_t)K[b] * 4);
+  }
+  const size_t o_it = tot, o_rn = a16(o_it + (size_t)count * 4), total = a16(o_rn + (size_t)count * 8) + 16;
+  char* tmp = nullptr;
+  CS_CUDA(cudaMallocAsync((void**)&tmp, total, st), "cudaMallocAsync tune outputs");
+  std::vector<MultiItem> group[8];
+  std::map<const PlanView*, int> dflt;  // each plan's default switch point
+  for (int64_t b = 0; b < count; ++b) {
+    const cs_plan_s* p = plans[b];
+    if (p->v.logN > kMaxLogNMulti) continue;
+    MultiItem it;
+    it.P = &p->v;
+    it.y = y_dev[b];
+    it.x = tmp + off[(size_t)b];
+    it.supp = (int*)(tmp + off[(size_t)b] + a16((size_t)K[b] * 16));
+    it.K = K[b];
+    it.t_switch = p->v.large ? multi_switch_big(p->v.logN) : plan_switch(p);
+    it.idx = (int)b;
+    it.cost = 0.0;
+    group[batch_group(p->v)].push_back(it);
+    dflt[&p->v] = it.t_switch;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cs_status r = CS_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = CS_ERR_CUDA;
+  BatchShape prev[8];  // what later calls would have used before this tuning
+  for (int gi = 0; gi < 8; ++gi) prev[gi] = batch_shape(dev, gi);
+  int nrec = 0;
+  for (int gi = 0; gi < 8 && r == CS_OK; ++gi) {
+    std::vector<MultiItem>& g = group[gi];
+    if (g.empty()) continue;
+    int err = 0;
+    const int occ = omp_multi_occupancy(g.data(), (int64_t)g.size(), CS_PATH_HYBRID, &err);
+    if (err || occ < 1) {
+      r = CS_ERR_CUDA;
+      break;
+    }
+    // one candidate: every instance at switch point ts (< 0: its default)
+    auto time_it = [&](int ctas, int ts) -> float {
+      for (MultiItem& it : g) {
+        it.t_switch = ts >= 0 ? ts : dflt[it.P];
+        it.cost = multi_cost(*it.P, it.K, it.t_switch, CS_PATH_HYBRID);
+      }
+      float best = -1.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaError_t e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess)
+          e = launch_omp_multi(g.data(), (int64_t)g.size(), rel_tol, CS_PATH_HYBRID, ctas, (int*)(tmp + o_it),
+                               (double*)(tmp + o_rn), plans[0]->v.status, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          cuda_fail(e, "omp_batched_tune");
+          return -1.f;
+        }
+        if (rep > 0 && (best < 0.f || ms < best)) best = ms;
+      }
+      return best;
+    };
+    BatchShape shp;
+    float best = time_it(0, -1);
+    if (best < 0.f) { r = CS_ERR_CUDA; break; }
+    for (int c = 1; c < occ; ++c) {  // fewer resident CTAs per SM
+      const float ms = time_it(c, -1);
+      if (ms < 0.f) { r = CS_ERR_CUDA; break; }
+      if (ms < 0.98f * best) { best = ms; shp.ctas_per_sm = c; }
+    }
+    if (r != CS_OK) break;
+    const bool big = gi & 1;
+    const int cands_big[] = {16, 64, 128}, cands_small[] = {32, 128};
+    const int* cands = big ? cands_big : cands_small;
+    const int nc = big ? 3 : 2;
+    for (int i = 0; i < nc; ++i) {
+      const float ms = time_it(shp.ctas_per_sm, cands[i]);
+      if (ms < 0.f) { r = CS_ERR_CUDA; break; }
+      if (ms < 0.98f * best) { best = ms; shp.t_switch = cands[i]; }
+    }
+    if (r != CS_OK) break;
+    set_batch_shape(dev, gi, shp);
+    if (nrec < cap) {
+      if (group_out) group_out[nrec] = gi;
+      if (ctas_out) ctas_out[nrec] = shp.ctas_per_sm;
+      if (tswitch_out) tswitch_out[nrec] = shp.t_switch;
+      if (ms_out) ms_out[nrec] = best;
+    }
+    ++nrec;
+  }
+  // The groups' launches run side by side in a cs_omp_batched call and share
+  // the SMs and L2, so the shapes measured per group are kept only if the
+  // whole call is faster with them than with the shapes it had before (and
+  // than with the tuned switch points alone).
+  if (r == CS_OK && nrec > 0) {
+    std::vector<void*> xs((size_t)count), ss((size_t)count);
+    for (int64_t b = 0; b < count; ++b) {
+      xs[(size_t)b] = tmp + off[(size_t)b];
+      ss[(size_t)b] = tmp + off[(size_t)b] + a16((size_t)K[b] * 16);
+    }
+    const cs_halt hh = {rel_tol, CS_PATH_HYBRID, -1, 0};
+    auto full_call = [&]() -> float {
+      float best = -1.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaError_t e = cudaEventRecord(e0, st);
+        if (e != cudaSuccess) return -1.f;
+        if (cs_omp_batched(plans, count, y_dev, K, &hh, xs.data(), (int32_t* const*)ss.data(), (int*)(tmp + o_it),
+                           (double*)(tmp + o_rn), st) != CS_OK)
+          return -1.f;
+        e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) return -1.f;
+        if (rep > 0 && (best < 0.f || ms < best)) best = ms;
+      }
+      return best;
+    };
+    BatchShape tuned[8], only_ts[8];
+    for (int gi = 0; gi < 8; ++gi) {
+      tuned[gi] = batch_shape(dev, gi);
+      only_ts[gi] = tuned[gi];
+      only_ts[gi].ctas_per_sm = prev[gi].ctas_per_sm;
+    }
+    auto install = [&](const BatchShape* v) { for (int gi = 0; gi < 8; ++gi) set_batch_shape(dev, gi, v[gi]); };
+    const float t_tuned = full_call();
+    install(only_ts);
+    const float t_ts = full_call();
+    install(prev);
+    const float t_prev = full_call();
+    if (t_tuned < 0.f || t_ts < 0.f || t_prev < 0.f) {
+      r = CS_ERR_CUDA;
+    } else if (t_tuned < 0.98f * t_prev && t_tuned <= t_ts) {
+      install(tuned);
+    } else if (t_ts < 0.98f * t_prev) {
+      install(only_ts);
+    }
+    // the records report what is stored
+    for (int i = 0; i < nrec && i < cap; ++i) {
+      const BatchShape v = batch_shape(dev, group_out ? group_out[i] : 0);
+      if (group_out && ctas_out) ctas_out[i] = v.ctas_per_sm;
+      if (group_out && tswitch_out) tswitch_out[i] = v.t_switch;
+    }
+  }
+  if (n_out) *n_out = nrec;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  const cudaError_t ef = cudaFreeAsync(tmp, st);
+  if (r != CS_OK) return r;
+  CS_CUDA(ef, "cudaFreeAsync tune outputs");
   return CS_OK;
 }
 

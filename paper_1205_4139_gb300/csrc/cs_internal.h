@@ -145,8 +145,11 @@ cudaError_t chain_twiddles(int logN, cudaStream_t st, const void** tw64, const v
 int multi_switch_big(int logN);
 double multi_cost(const PlanView& P, int K, int t_switch, int path);
 size_t omp_multi_smem(const MultiItem* it, int64_t n, int path);
-cudaError_t launch_omp_multi(MultiItem* it, int64_t n, double rel_tol, int path, int* iters_out, double* res_out,
-                             int* status, cudaStream_t st);
+// ctas_per_sm: resident CTAs per SM (0: as many as fit)
+cudaError_t launch_omp_multi(MultiItem* it, int64_t n, double rel_tol, int path, int ctas_per_sm, int* iters_out,
+                             double* res_out, int* status, cudaStream_t st);
+// CTAs per SM a launch of these instances (one element type and residence) can hold
+int omp_multi_occupancy(const MultiItem* it, int64_t n, int path, int* err);
 
 // large plans (cs_large.cu)
 cudaError_t large_tables(const PlanView& P, void* lt64, void* lt32, cudaStream_t st);

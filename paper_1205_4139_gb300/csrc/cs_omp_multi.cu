@@ -533,9 +533,24 @@ size_t smem_t(const Sizes& z, int path) {
   return z.Nsm == 0 ? slayout<E>(z.Kmax).total : mlayout<E>(z.Nsm, z.Kmax, path).total;
 }
 
+// CTAs per SM the launch of these instances can hold (shared memory,
+// registers), for the kernel of their residence.
 template <class E>
-cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int* iters_out, double* res_out, int* status,
-                    cudaStream_t st) {
+int occ_t(const MultiItem* it, int64_t n, int path, int* err) {
+  const Sizes z = sizes_of(it, n);
+  const bool seq = z.Nsm == 0;
+  const size_t smem = smem_t<E>(z, path);
+  const void* kfn = seq ? (const void*)omp_seq_kernel<E> : (const void*)omp_multi_kernel<E>;
+  cudaError_t e = raise_smem_limit(kfn, smem);
+  int occ = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, seq ? kSThreads : kMThreads, smem);
+  *err = (int)e;
+  return e == cudaSuccess ? occ : 0;
+}
+
+template <class E>
+cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int ctas_per_sm, int* iters_out,
+                    double* res_out, int* status, cudaStream_t st) {
   using W = typename FT<E>::W;
   std::stable_sort(it, it + n, [](const MultiItem& u, const MultiItem& v) { return u.cost > v.cost; });
   const Sizes z = sizes_of(it, n);
@@ -552,6 +567,9 @@ cudaError_t multi_t(MultiItem* it, int64_t n, double rel_tol, int path, int* ite
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, threads, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
+  // resident CTAs: all that fit, or the tuned number per SM (fewer CTAs keep
+  // fewer instance vectors in flight, which can keep them in L2)
+  if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
   const int64_t need = seq ? n : (n + 1) / 2, cap = (int64_t)occ * sms;
   const int grid = (int)(need < cap ? need : cap);
   const int per = seq ? 1 : 2;  // instance slots per CTA
@@ -659,15 +677,23 @@ size_t omp_multi_smem(const MultiItem* it, int64_t n, int path) {
   return P.fp32 ? smem_t<float>(z, path) : smem_t<double>(z, path);
 }
 
-cudaError_t launch_omp_multi(MultiItem* it, int64_t n, double rel_tol, int path, int* iters_out, double* res_out,
-                             int* status, cudaStream_t st) {
+cudaError_t launch_omp_multi(MultiItem* it, int64_t n, double rel_tol, int path, int ctas_per_sm, int* iters_out,
+                             double* res_out, int* status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const PlanView& P = *it[0].P;
   if (P.dft)
-    return P.fp32 ? multi_t<float2>(it, n, rel_tol, path, iters_out, res_out, status, st)
-                  : multi_t<double2>(it, n, rel_tol, path, iters_out, res_out, status, st);
-  return P.fp32 ? multi_t<float>(it, n, rel_tol, path, iters_out, res_out, status, st)
-                : multi_t<double>(it, n, rel_tol, path, iters_out, res_out, status, st);
+    return P.fp32 ? multi_t<float2>(it, n, rel_tol, path, ctas_per_sm, iters_out, res_out, status, st)
+                  : multi_t<double2>(it, n, rel_tol, path, ctas_per_sm, iters_out, res_out, status, st);
+  return P.fp32 ? multi_t<float>(it, n, rel_tol, path, ctas_per_sm, iters_out, res_out, status, st)
+                : multi_t<double>(it, n, rel_tol, path, ctas_per_sm, iters_out, res_out, status, st);
+}
+
+int omp_multi_occupancy(const MultiItem* it, int64_t n, int path, int* err) {
+  *err = 0;
+  if (n <= 0) return 0;
+  const PlanView& P = *it[0].P;
+  if (P.dft) return P.fp32 ? occ_t<float2>(it, n, path, err) : occ_t<double2>(it, n, path, err);
+  return P.fp32 ? occ_t<float>(it, n, path, err) : occ_t<double>(it, n, path, err);
 }
 
 }  // namespace csf

@@ -242,3 +242,36 @@ def test_refusals():
         binding.omp_batched([small], [torch.zeros(8, dtype=torch.float64, device="cuda")], [9])
     with pytest.raises(ValueError):  # y of the wrong length
         binding.omp_batched([small], [torch.zeros(7, dtype=torch.float64, device="cuda")], [2])
+
+
+def test_batch_tuner_shapes_and_results():
+    """cs_omp_batched_tune on a mix of residences and element types: one
+    record per launch group present, shapes within their candidate sets, and
+    cs_omp_batched with the stored shapes still matches the oracle (supports
+    to the first near tie, noiseless x); count = 0 forgets the shapes."""
+    specs = [("wht", "fp32", 4096, 1024, 20, None), ("dft", "fp32", 2048, 512, 24, None),
+             ("dft", "fp32", 1 << 14, 2048, 30, None), ("wht", "fp32", 1 << 15, 4096, 24, None)] * 6
+    plans, ys, Ks, insts = build(specs, 21)
+    bt = binding.Batch(plans, ys, Ks)
+    try:
+        recs = binding.batch_tune(bt)
+        assert sorted(r["group"] for r in recs) == ["dft fp32 global", "dft fp32 shared", "wht fp32 global",
+                                                    "wht fp32 shared"]
+        for r in recs:
+            assert r["ctas_per_sm"] >= 0 and r["ms"] > 0
+            assert r["t_switch"] in ((-1, 16, 64, 128) if r["group"].endswith("global") else (-1, 32, 128))
+        bt.run()
+        torch.cuda.synchronize()
+        compared = 0
+        for b in range(len(specs)):
+            compared += check_against_oracle(insts[b], bt.x[b].cpu().numpy(), bt.supp[b].cpu().numpy(),
+                                             int(bt.iters[b]), float(bt.resnorm[b]), True)
+        assert compared >= 8
+        assert plans[0].device_error() == 0
+    finally:
+        binding.batch_untune()
+    # forgotten: small instances equal cs_omp at the plan's switch point again
+    bt.run()
+    torch.cuda.synchronize()
+    x, s, it, rn = plans[0].omp(ys[0][None], Ks[0])
+    assert torch.equal(bt.supp[0], s[0]) and torch.equal(bt.x[0], x[0])
