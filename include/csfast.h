@@ -295,8 +295,16 @@ cs_status cs_omp_batched_tune(const cs_plan_t* plans, int64_t count, const void*
  * the final support in ascending column order (-1 / 0 past its size),
  * iters_dev (iterations run), resnorm_dev (||r|| / ||y||).
  * Large plans (N > 8192) run the same steps with the correlation over the
- * whole GPU and the top-k over N in two stages (per tile, then per instance).
- * Limits: 1 <= K, 2K <= M (SP), 3K <= M (CoSaMP), K <= 128. */
+ * whole GPU and the top-k over N in two stages (per tile, then per instance);
+ * when a least-squares set can exceed 96 columns (SP: K > 48, CoSaMP:
+ * K > 32) they solve the normal equations by FP64 conjugate gradients, one
+ * thread-block cluster of 4 to 16 CTAs per instance, Gram products read off
+ * the FP64 kernel vector, from the previous coefficients, to a relative
+ * residual of 1e-12 (at most 2m iterations for m columns, 64 to 4000); a
+ * column set whose columns are dependent is then solved only as far as
+ * the iterations reach, instead of dropping the dependent column.
+ * Limits: 1 <= K, 2K <= M (SP), 3K <= M (CoSaMP), K <= 128 for N <= 8192,
+ * K <= 1024 for larger N. */
 cs_status cs_sp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,
                 void* x_dev, int32_t* supp_dev, int32_t* iters_dev, double* resnorm_dev, void* stream);
 cs_status cs_cosamp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,

@@ -72,13 +72,23 @@ extern "C" const char* cs_last_error(void) { return g_err; }
 
 namespace csf {
 cudaError_t raise_smem_limit(const void* func, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
   static std::mutex mu;
-  static std::map<std::pair<int, const void*>, size_t> limit;
+  static std::map<std::pair<int, const void*>, size_t> limit, static_bytes;
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
-  size_t& cur = limit[std::make_pair(dev, func)];
+  const auto key = std::make_pair(dev, func);
+  // without the attribute a launch may use 48 KB of shared memory in all,
+  // the kernel's static shared memory included
+  auto it = static_bytes.find(key);
+  if (it == static_bytes.end()) {
+    cudaFuncAttributes fa;
+    const cudaError_t ea = cudaFuncGetAttributes(&fa, func);
+    if (ea != cudaSuccess) return ea;
+    it = static_bytes.emplace(key, fa.sharedSizeBytes).first;
+  }
+  if (bytes + it->second <= 48 * 1024) return cudaSuccess;
+  size_t& cur = limit[key];
   if (cur >= bytes) return cudaSuccess;
   const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) cur = bytes;
@@ -913,7 +923,7 @@ static cs_status pursuit_call(int algo, cs_plan_t plan, const void* y_dev, int64
                               double* resnorm_dev, void* stream) {
   if (!plan || batch < 0 || K < 1) return CS_ERR_INVALID;
   if ((algo == 0 ? 2 : 3) * (int64_t)K > plan->v.M) return CS_ERR_INVALID;
-  if (K > 128) return CS_ERR_UNSUPPORTED;
+  if (K > (plan->v.large ? kMaxPursuitKLarge : kMaxPursuitK)) return CS_ERR_UNSUPPORTED;
   if (plan->v.large && batch > kMaxLargeBatch) return CS_ERR_UNSUPPORTED;
   cs_halt h = {1e-6, CS_PATH_HYBRID, -1, 0};
   if (halt) h = *halt;

@@ -12,6 +12,8 @@ constexpr int kMaxLogNLarge = 24;  // four-step transforms through global memory
 constexpr int kMaxK = 1024;
 constexpr int kMaxKLarge = 4096;       // large plans: the factor lives in global memory
 constexpr int kMaxLargeBatch = 65535;  // large plans: instances per call
+constexpr int kMaxPursuitK = 128;       // SP / CoSaMP, N <= 8192: one CTA appends the columns
+constexpr int kMaxPursuitKLarge = 1024; // SP / CoSaMP, large plans: conjugate-gradient least squares
 constexpr int kMaxLogNMulti = 16;      // cs_omp_batched: one CTA per instance up to N = 2^16
 
 // Type-erased view of a plan's device tables.

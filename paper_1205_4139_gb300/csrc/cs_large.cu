@@ -29,6 +29,7 @@
 #include <cmath>
 
 #include "cs_blocks.cuh"
+#include "cs_cg.cuh"
 #include "cs_internal.h"
 #include "cs_ls.cuh"
 #include "cs_select.cuh"
@@ -1356,6 +1357,11 @@ constexpr int kSelTile = kLT * 8;
 struct LPExtra {  // per instance, beside the LState done flag
   int ns, m, it, pad;
   double ynorm2, rn2, rn2_new, ls_rn2;
+  // least squares by conjugate gradients (large K): the set Tq[0..mq), the
+  // next solver call's mode (0 none, 1 solve, 2 quadratic form), whether xq
+  // holds a start, the solver's iterations so far, the quadratic form
+  int mq, cgmode, warm, cgit;
+  double qf;
 };
 
 template <class E>
@@ -1385,7 +1391,24 @@ struct LPArgs {
   LPExtra* ex;
   double* ypart;
   int nyp;
+  // conjugate-gradient least squares (lq != 0): column set, right-hand side
+  // h_0(T) and solution / start, [batch][mm] each
+  int lq;
+  int* Tq;
+  W* rq;
+  W* xq;
+  int cg_max;
+  double cg_tol;
+  // FP32 plans: h_0 = Phi^H y once more in FP64 ([batch][N]), the right-hand
+  // sides of the least squares (NULL: h0 is already FP64)
+  const W* h64;
 };
+
+// (Phi^H y)(j) in FP64 for the least squares
+template <class E>
+__device__ __forceinline__ typename FT<E>::W lp_rhs(const LPArgs<E>& a, int64_t b, int j) {
+  return a.h64 ? a.h64[b * (int64_t)a.P.N + j] : to_w(a.h0[b * (int64_t)a.P.N + j]);
+}
 
 __host__ __device__ inline int lp_mmax(int K, int algo) { return algo == 0 ? 2 * K : 3 * K; }
 
@@ -1678,11 +1701,296 @@ __global__ void __launch_bounds__(kLT) lp_step_kernel(LPArgs<E> a, int phase) {
   if (threadIdx.x == 0) a.ex[b] = X;
 }
 
+// ---------------------------------- SP and CoSaMP with large column sets
+// The least squares of an iteration (on up to 2K or 3K columns) by the
+// cluster conjugate-gradient solver of cs_cg.cuh instead of appending the
+// columns one CTA at a time.  Per iteration the host queues, after the
+// correlation and the top-k: lq_form (the set T and its right-hand side,
+// the previous coefficients as the start), lq_cg (b = LS on T), lq_prune
+// (the K largest |b|; SP: the second set T_new, CoSaMP: the pruned estimate),
+// lq_cg again (SP: x_new = LS on T_new from b's values; CoSaMP: the
+// quadratic form x^H G x of the pruned estimate) and lq_accept (the stop
+// rules).  Same steps, order, tie rules and stop rules as lp_step_kernel.
+
+// The accepted support and coefficients (ns entries, ascending columns).
+template <class E>
+__device__ void lp_set_support(const LPArgs<E>& a, int64_t b, LPExtra& X, const int* cols,
+                               const typename FT<E>::W* coef, int ns) {
+  using W = typename FT<E>::W;
+  const int K = a.K;
+  int* S = a.S + b * K;
+  W* xs = a.xs + b * K;
+  E* xsw = a.xsw + b * K;
+  uint32_t* bb = a.bits + b * (int64_t)(a.P.N >> 5);
+  E* xz = a.xz ? a.xz + b * (int64_t)a.P.N : nullptr;
+  for (int k = threadIdx.x; k < X.ns; k += kLT) {  // the old support leaves bits and zf(x)
+    const int j = S[k];
+    if (xz) xz[j] = zero<E>();
+    atomicAnd(bb + (j >> 5), ~(1u << (j & 31)));
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += kLT) {
+    const int j = k < ns ? cols[k] : 0;
+    const W v = k < ns ? coef[k] : W{};
+    S[k] = j;
+    xs[k] = v;
+    xsw[k] = from_w<E>(v);
+    if (k < ns) {
+      if (xz) xz[j] = from_w<E>(v);
+      atomicOr(bb + (j >> 5), 1u << (j & 31));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) X.ns = ns;
+  __syncthreads();
+}
+
+// phase 0: ||y||^2 (and SP: T_0 = top_K(h_0) to solve); phase 1: T = the
+// support joined with the selection (both ascending, no duplicates), the
+// start = the support's coefficients, zero on the new columns.
+template <class E>
+__global__ void __launch_bounds__(kLT) lq_form_kernel(LPArgs<E> a, int phase) {
+  using W = typename FT<E>::W;
+  __shared__ LPExtra X;
+  __shared__ double red[32 * 1 + 1];
+  const int64_t b = blockIdx.x;
+  if (a.st[b].done) return;
+  const int K = a.K, mm = lp_mmax(K, a.algo);
+  const Grp g = whole_block();
+  if (threadIdx.x == 0) X = a.ex[b];
+  __syncthreads();
+  int* T = a.Tq + b * (int64_t)mm;
+  W* rq = a.rq + b * (int64_t)mm;
+  W* xq = a.xq + b * (int64_t)mm;
+  const int* sel = a.sel + b * (int64_t)a.kmax;
+  if (phase == 0) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < a.nyp; i += kLT) t += a.ypart[b * a.nyp + i];
+    double tt[1] = {t};
+    group_sum(g, tt, red);
+    if (threadIdx.x == 0) {
+      X.ynorm2 = tt[0];
+      X.rn2 = tt[0];
+      X.ns = 0;
+      X.it = 0;
+      X.cgmode = 0;
+      X.cgit = 0;
+    }
+    __syncthreads();
+    if (!(X.ynorm2 > 0.0) || K == 0) {
+      lp_outputs(a, b, X);
+    } else if (a.algo == 0) {
+      for (int i = threadIdx.x; i < K; i += kLT) {
+        T[i] = sel[i];
+        rq[i] = lp_rhs(a, b, sel[i]);
+      }
+      if (threadIdx.x == 0) {
+        X.mq = K;
+        X.cgmode = 1;
+        X.warm = 0;
+      }
+    }
+  } else {
+    const int ns = X.ns, kk = a.algo == 0 ? K : 2 * K;
+    const int* S = a.S + b * K;
+    const W* xs = a.xs + b * K;
+    if (threadIdx.x == 0) {
+      int i = 0, j = 0, o = 0;
+      while (i < ns || j < kk) {
+        if (j >= kk || (i < ns && S[i] < sel[j])) {
+          T[o] = S[i];
+          xq[o++] = xs[i++];
+        } else if (i < ns && S[i] == sel[j]) {
+          T[o] = S[i];
+          xq[o++] = xs[i++];
+          ++j;
+        } else {
+          T[o] = sel[j++];
+          xq[o++] = W{};
+        }
+      }
+      X.mq = o;
+      X.cgmode = 1;
+      X.warm = ns > 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < X.mq; i += kLT) rq[i] = lp_rhs(a, b, T[i]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.ex[b] = X;
+}
+
+// One cluster of G CTAs per instance: the solve (mode 1) or the quadratic
+// form (mode 2) of cs_cg.cuh on the instance's set.
+template <class E, int G>
+__global__ void __launch_bounds__(kLT) lq_cg_kernel(LPArgs<E> a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  cgx::cluster_group cl = cgx::this_cluster();
+  const int64_t b = blockIdx.x / G;
+  // every CTA of the cluster reads the same flags: all leave or none
+  if (a.st[b].done) return;
+  const int mode = a.ex[b].cgmode;
+  if (mode == 0) return;
+  const int m = a.ex[b].mq, mm = lp_mmax(a.K, a.algo);
+  PlanDev<E> pd;
+  pd.N = a.P.N;
+  pd.logN = a.P.logN;
+  pd.M = a.P.M;
+  pd.slot = a.P.slot;
+  pd.tw = nullptr;
+  pd.c = a.P.c;
+  pd.c64 = a.P.c64;
+  pd.cfmt = a.P.cfmt;
+  pd.ci = a.P.ci;
+  using W = typename FT<E>::W;
+  W* xq = a.xq + b * (int64_t)mm;
+  const CgResult r = cg_cluster<E, G>(cl, pd, a.Tq + b * (int64_t)mm, m, a.rq + b * (int64_t)mm,
+                                      (mode == 2 || a.ex[b].warm) ? xq : nullptr, xq, mode, a.cg_tol,
+                                      a.cg_max, sm, mm);
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    if (mode == 1) {
+      a.ex[b].ls_rn2 = a.ex[b].ynorm2 - r.bh;
+      a.ex[b].cgit += r.iters;
+    } else {
+      a.ex[b].qf = r.q;
+    }
+  }
+}
+
+// phase 0 (SP): the first support is T_0 with its solution.  phase 1: the K
+// largest |b| (ties to the lower index) -> SP: T_new to solve from b's
+// values, unless it repeats the accepted support; CoSaMP: the pruned
+// estimate, its quadratic form to be taken next.
+template <class E>
+__global__ void __launch_bounds__(kLT) lq_prune_kernel(LPArgs<E> a, int phase) {
+  using W = typename FT<E>::W;
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ LPExtra X;
+  __shared__ double red[32 * 1 + 1];
+  __shared__ int hist[260];
+  __shared__ int scr[34];
+  __shared__ int same;
+  const int64_t b = blockIdx.x;
+  if (a.st[b].done) return;
+  const int K = a.K, mm = lp_mmax(K, a.algo);
+  const Grp g = whole_block();
+  if (threadIdx.x == 0) X = a.ex[b];
+  __syncthreads();
+  int* T = a.Tq + b * (int64_t)mm;
+  W* rq = a.rq + b * (int64_t)mm;
+  W* xq = a.xq + b * (int64_t)mm;
+  const double tol2 = a.rel_tol * a.rel_tol;
+  if (phase == 0) {
+    lp_set_support(a, b, X, T, xq, X.mq);
+    if (threadIdx.x == 0) {
+      X.rn2 = X.ls_rn2;
+      X.cgmode = 0;
+    }
+    __syncthreads();
+    if (X.it >= a.max_iter || X.rn2 < tol2 * X.ynorm2) lp_outputs(a, b, X);
+    if (threadIdx.x == 0) a.ex[b] = X;
+    return;
+  }
+  const int m = X.mq, kp = K < m ? K : m;
+  unsigned long long* sk = (unsigned long long*)sm;
+  int* pos = (int*)(sm + al16((size_t)mm * sizeof(unsigned long long)));
+  int* tn = pos + kp;
+  W* vn = (W*)(sm + al16((size_t)mm * sizeof(unsigned long long)) + al16((size_t)2 * K * sizeof(int)));
+  for (int i = threadIdx.x; i < m; i += kLT) sk[i] = sel_key(norm2(xq[i]));
+  __syncthreads();
+  group_topk(g, sk, m, kp, pos, hist, scr);  // ascending positions
+  for (int i = threadIdx.x; i < kp; i += kLT) {
+    tn[i] = T[pos[i]];
+    vn[i] = xq[pos[i]];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kp; i += kLT) {
+    T[i] = tn[i];
+    xq[i] = vn[i];
+  }
+  if (a.algo == 0) {
+    if (threadIdx.x == 0) {
+      const int* S = a.S + b * K;
+      bool sm_ = kp == X.ns;
+      for (int i = 0; sm_ && i < kp; ++i) sm_ = tn[i] == S[i];
+      same = sm_;
+    }
+    __syncthreads();
+    if (same) {
+      if (threadIdx.x == 0) {
+        X.rn2_new = X.rn2;
+        X.cgmode = 0;
+      }
+    } else {
+      for (int i = threadIdx.x; i < kp; i += kLT) rq[i] = lp_rhs(a, b, tn[i]);
+      if (threadIdx.x == 0) {
+        X.mq = kp;
+        X.cgmode = 1;
+        X.warm = 1;
+        X.rn2_new = -1.0;  // taken from the solve
+      }
+    }
+  } else {
+    // ||y - Phi x||^2 = ||y||^2 - 2 Re x^H h_0(S) + x^H G_S x; the quadratic
+    // form comes from the next solver call
+    double acc[1] = {0.0};
+    for (int i = threadIdx.x; i < kp; i += kLT) acc[0] += re(cmul(vn[i], lp_rhs(a, b, tn[i])));
+    group_sum(g, acc, red);
+    if (threadIdx.x == 0) {
+      X.rn2_new = X.ynorm2 - 2.0 * acc[0];
+      X.mq = kp;
+      X.cgmode = 2;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.ex[b] = X;
+}
+
+template <class E>
+__global__ void __launch_bounds__(kLT) lq_accept_kernel(LPArgs<E> a) {
+  __shared__ LPExtra X;
+  const int64_t b = blockIdx.x;
+  if (a.st[b].done) return;
+  const int mm = lp_mmax(a.K, a.algo);
+  if (threadIdx.x == 0) {
+    X = a.ex[b];
+    if (X.cgmode == 1) X.rn2_new = X.ls_rn2;       // SP: LS on T_new
+    else if (X.cgmode == 2) X.rn2_new += X.qf;      // CoSaMP: + x^H G x
+    X.it = X.it + 1;
+  }
+  __syncthreads();
+  const double tol2 = a.rel_tol * a.rel_tol;
+  bool stop = false;
+  if (!(X.rn2_new < X.rn2)) {
+    stop = true;  // keep the previous iterate
+  } else {
+    lp_set_support(a, b, X, a.Tq + b * (int64_t)mm, a.xq + b * (int64_t)mm, X.mq);
+    if (threadIdx.x == 0) X.rn2 = X.rn2_new;
+    __syncthreads();
+  }
+  if (!stop && (X.it >= a.max_iter || X.rn2 < tol2 * X.ynorm2)) stop = true;
+  if (stop) lp_outputs(a, b, X);
+  if (threadIdx.x == 0) {
+    X.cgmode = 0;
+    a.ex[b] = X;
+  }
+}
+
+template <class E>
+__global__ void __launch_bounds__(kLT) widen_kernel(const E* __restrict__ in, int64_t n,
+                                                    typename FT<E>::W* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)kLT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kLT) out[i] = to_w(in[i]);
+}
+
 template <class E>
 struct LPWs {
-  size_t st, ex, h0, H, T, Z, xz, bits, S, xs, xsw, ck, cj, sel, B, yp, total;
+  size_t st, ex, h0, H, T, Z, xz, bits, S, xs, xsw, ck, cj, sel, B, yp, Tq, rq, xq, h64, T64, y64, total;
   int ntiles, kmax, nyp;
 };
+
+// Column sets larger than this take the conjugate-gradient least squares.
+constexpr int kLqMin = 96;
+__host__ __device__ inline bool lp_uses_cg(int K, int algo) { return lp_mmax(K, algo) > kLqMin; }
 
 template <class E>
 LPWs<E> lp_ws(const PlanView& Pv, int K, int algo, int fast, int64_t batch) {
@@ -1712,10 +2020,80 @@ LPWs<E> lp_ws(const PlanView& Pv, int K, int algo, int fast, int64_t batch) {
   L.ck = o;   o = al16(o + (size_t)batch * L.ntiles * L.kmax * sizeof(U));
   L.cj = o;   o = al16(o + (size_t)batch * L.ntiles * L.kmax * sizeof(int));
   L.sel = o;  o = al16(o + (size_t)batch * L.kmax * sizeof(int));
-  L.B = o;    o = al16(o + (size_t)batch * (((size_t)mm * (mm + 1)) / 2) * sizeof(W));
+  const bool lq = lp_uses_cg(K, algo);
+  L.B = o;    o = al16(o + (lq ? 0 : (size_t)batch * (((size_t)mm * (mm + 1)) / 2) * sizeof(W)));
   L.yp = o;   o = al16(o + (size_t)batch * L.nyp * sizeof(double));
+  L.Tq = o;   o = al16(o + (lq ? (size_t)batch * mm * sizeof(int) : 0));
+  L.rq = o;   o = al16(o + (lq ? (size_t)batch * mm * sizeof(W) : 0));
+  L.xq = o;   o = al16(o + (lq ? (size_t)batch * mm * sizeof(W) : 0));
+  const bool h64 = lq && sizeof(E) != sizeof(W);
+  L.h64 = o;  o = al16(o + (h64 ? (size_t)batch * N * sizeof(W) : 0));
+  L.T64 = o;  o = al16(o + (h64 ? (size_t)batch * N * sizeof(W) : 0));
+  L.y64 = o;  o = al16(o + (h64 ? (size_t)batch * Pv.M * sizeof(W) : 0));
   L.total = o;
   return L;
+}
+
+// Conjugate-gradient launches: one cluster of G CTAs per instance.  A CTA
+// asks for more than half of an SM's shared memory when G >= 8, so that the
+// cluster spreads over G SMs (the solver is bound by the FP64 pipe).
+template <class E, int G>
+cudaError_t lq_cg_launch(const LPArgs<E>& a, int64_t batch, cudaStream_t s, bool probe_only, int* ok) {
+  using W = typename FT<E>::W;
+  const int mm = lp_mmax(a.K, a.algo);
+  size_t smem = cg_smem_bytes<W>(mm, G);
+  if (G >= 8 && smem < (size_t)116 * 1024) smem = (size_t)116 * 1024;
+  auto kern = lq_cg_kernel<E, G>;
+  cudaError_t e = allow_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  if (G > 8 && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+    return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(batch * G));
+  cfg.blockDim = dim3(kLT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = G;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (probe_only) {
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      n = 0;
+    }
+    *ok = n > 0;
+    return cudaSuccess;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <class E>
+cudaError_t lq_cg(const LPArgs<E>& a, int64_t batch, int G, cudaStream_t s) {
+  int ok = 0;
+  switch (G) {
+    case 16: return lq_cg_launch<E, 16>(a, batch, s, false, &ok);
+    case 8: return lq_cg_launch<E, 8>(a, batch, s, false, &ok);
+    default: return lq_cg_launch<E, 4>(a, batch, s, false, &ok);
+  }
+}
+
+// CTAs per cluster: 16 for large sets where the GPU can place such a
+// cluster, else 8; 4 for small sets.
+template <class E>
+int lq_cluster_size(const LPArgs<E>& a, int64_t batch, cudaStream_t s) {
+  const int mm = lp_mmax(a.K, a.algo);
+  if (mm < 256) return 4;
+  if (mm >= 768) {
+    int ok = 0;
+    if (lq_cg_launch<E, 16>(a, batch, s, true, &ok) == cudaSuccess && ok) return 16;
+  }
+  return 8;
 }
 
 template <class E>
@@ -1757,6 +2135,16 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
   a.B = (W*)(w + L.B);
   a.ypart = (double*)(w + L.yp);
   a.nyp = L.nyp;
+  a.lq = lp_uses_cg(q.K, q.algo);
+  a.Tq = a.lq ? (int*)(w + L.Tq) : nullptr;
+  a.rq = a.lq ? (W*)(w + L.rq) : nullptr;
+  a.xq = a.lq ? (W*)(w + L.xq) : nullptr;
+  a.h64 = (a.lq && sizeof(E) != sizeof(W)) ? (const W*)(w + L.h64) : nullptr;
+  {
+    const int mm = lp_mmax(q.K, q.algo);
+    a.cg_max = 2 * mm < 64 ? 64 : (2 * mm > 4000 ? 4000 : 2 * mm);
+    a.cg_tol = 1e-12;
+  }
   const size_t Nv = (size_t)batch * P.N * sizeof(E);
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.st, 0, (size_t)batch * sizeof(LState), s)) != cudaSuccess) return e;
@@ -1768,9 +2156,10 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
   if (a.xz && (e = cudaMemsetAsync(a.xz, 0, Nv, s)) != cudaSuccess) return e;
   const size_t tile_smem = al16((size_t)kSelTile * sizeof(U)) + al16((size_t)a.kmax * sizeof(int)) + 300 * sizeof(int);
   const size_t merge_smem = al16((size_t)a.kmax * sizeof(int)) + 300 * sizeof(int);
-  const size_t step_smem = lp_layout<E>(q.K, q.algo).total;
+  const size_t step_smem = lp_uses_cg(q.K, q.algo) ? 0 : lp_layout<E>(q.K, q.algo).total;
   if ((e = allow_smem(lp_tile_kernel<E>, tile_smem)) != cudaSuccess) return e;
-  if ((e = allow_smem(lp_step_kernel<E>, step_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(lp_merge_kernel<E>, merge_smem)) != cudaSuccess) return e;
+  if (step_smem && (e = allow_smem(lp_step_kernel<E>, step_smem)) != cudaSuccess) return e;
   const double isq = inv_sqrt_n(P.logN);
   const dim3 tgrid((unsigned)L.ntiles, (unsigned)batch);
   // h_0 = Phi^H y by one transform, and ||y||^2
@@ -1780,11 +2169,41 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
   if ((e = run_row<E, DFT, SK_H>(P, T, DFT, isq, a.h0, nullptr, nullptr, nullptr, nullptr, 0, a.st, batch, s)) !=
       cudaSuccess)
     return e;
+  if (a.h64) {  // the same correlation in FP64 for the least squares' right-hand sides
+    const LDev<W> P64 = ldev<W>(Pv);
+    W* y64 = (W*)(w + L.y64);
+    const int64_t ny = batch * (int64_t)P.M;
+    if (ny > 0) {
+      widen_kernel<E><<<(unsigned)((ny + kLT - 1) / kLT < 4096 ? (ny + kLT - 1) / kLT : 4096), kLT, 0, s>>>(a.y, ny,
+                                                                                                        y64);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = run_col<W, DFT, LD_ZF>(P64, y64, P.M, (W*)(w + L.T64), a.st, batch, s)) != cudaSuccess) return e;
+    if ((e = run_row<W, DFT, SK_H>(P64, (const W*)(w + L.T64), DFT, isq, (W*)a.h64, nullptr, nullptr, nullptr,
+                                   nullptr, 0, a.st, batch, s)) != cudaSuccess)
+      return e;
+  }
   if (q.algo == 0) {  // SP's first support: top_K(h_0)
     lp_tile_kernel<E><<<tgrid, kLT, tile_smem, s>>>(a, a.h0, q.K, 0);
     lp_merge_kernel<E><<<(unsigned)batch, kLT, merge_smem, s>>>(a, q.K);
   }
-  lp_step_kernel<E><<<(unsigned)batch, kLT, step_smem, s>>>(a, 0);
+  int G = 0;
+  size_t prune_smem = 0;
+  if (a.lq) {
+    const int mm = lp_mmax(q.K, q.algo);
+    G = lq_cluster_size<E>(a, batch, s);
+    prune_smem = al16((size_t)mm * sizeof(unsigned long long)) + al16((size_t)2 * q.K * sizeof(int)) +
+                 (size_t)q.K * sizeof(W);
+    if ((e = allow_smem(lq_prune_kernel<E>, prune_smem)) != cudaSuccess) return e;
+    lq_form_kernel<E><<<(unsigned)batch, kLT, 0, s>>>(a, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (q.algo == 0) {
+      if ((e = lq_cg<E>(a, batch, G, s)) != cudaSuccess) return e;
+      lq_prune_kernel<E><<<(unsigned)batch, kLT, prune_smem, s>>>(a, 0);
+    }
+  } else {
+    lp_step_kernel<E><<<(unsigned)batch, kLT, step_smem, s>>>(a, 0);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int kk = q.algo == 0 ? q.K : 2 * q.K;
   for (int it = 0; it < q.max_iter; ++it) {
@@ -1804,7 +2223,20 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
     }
     lp_tile_kernel<E><<<tgrid, kLT, tile_smem, s>>>(a, H, kk, q.algo == 0);
     lp_merge_kernel<E><<<(unsigned)batch, kLT, merge_smem, s>>>(a, kk);
-    lp_step_kernel<E><<<(unsigned)batch, kLT, step_smem, s>>>(a, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.lq) {
+      // every launch is checked at once: a kernel that failed to start
+      // would leave the next one working on the previous step's state
+      lq_form_kernel<E><<<(unsigned)batch, kLT, 0, s>>>(a, 1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = lq_cg<E>(a, batch, G, s)) != cudaSuccess) return e;
+      lq_prune_kernel<E><<<(unsigned)batch, kLT, prune_smem, s>>>(a, 1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = lq_cg<E>(a, batch, G, s)) != cudaSuccess) return e;
+      lq_accept_kernel<E><<<(unsigned)batch, kLT, 0, s>>>(a);
+    } else {
+      lp_step_kernel<E><<<(unsigned)batch, kLT, step_smem, s>>>(a, 1);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

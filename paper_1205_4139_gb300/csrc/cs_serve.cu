@@ -211,7 +211,7 @@ cs_status check_request(const cs_request* q) {
     if (q->K > (q->N > (int64_t(1) << kMaxLogN) ? kMaxKLarge : kMaxK)) return CS_ERR_UNSUPPORTED;
   } else if (q->algo == CS_ALGO_COSAMP || q->algo == CS_ALGO_SP) {
     if (q->K < 1 || (q->algo == CS_ALGO_SP ? 2 : 3) * (int64_t)q->K > q->M) return CS_ERR_INVALID;
-    if (q->K > 128) return CS_ERR_UNSUPPORTED;
+    if (q->K > (q->N > (int64_t(1) << kMaxLogN) ? kMaxPursuitKLarge : kMaxPursuitK)) return CS_ERR_UNSUPPORTED;
   } else {
     return CS_ERR_INVALID;
   }
