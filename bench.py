@@ -520,18 +520,19 @@ def _serving_gen(req):
     return synth.serving_instance(req)
 
 
-def serving(n_req: int, rate: float = 2000.0, workers: int = 8, budget_gb: float = 64.0):
+def serving(n_req: int, rate: float = 2000.0, workers: int = 16, budget_gb: float = 64.0):
     """The serving workload: Poisson arrivals at 2000 requests/s, N = 2^14 ..
     2^20, M = N/8, K = 32 .. 1024, partial WHT or DFT by a coin, FP32, OMP
-    (hybrid switch) or CoSaMP by a coin (CoSaMP's K capped at 128, its limit
-    in the library), each request with its own Omega, replayed in real time
-    into the request runtime (cs_server_*) with `workers` streams and a
-    device-memory budget; latency = completion - arrival.  The same requests
-    are then replayed at half the throughput measured at the offered rate
-    (a sustainable rate) for the unsaturated latency.  One untimed replay of
-    all requests at once comes first: the first solves of each plan size in
-    a process pay one-off costs (growing the stream-ordered memory pool,
-    first launches of each kernel) that a running server has paid."""
+    (hybrid switch) or CoSaMP by a coin (CoSaMP's K capped at M/3, the most
+    its least squares allow), each request with its own Omega, replayed in
+    real time into the request runtime (cs_server_*) with `workers` streams
+    and a device-memory budget; latency = completion - arrival.  The same
+    requests are then replayed at half the throughput measured at the
+    offered rate (a sustainable rate) for the unsaturated latency.  An
+    untimed replay of the first requests at once comes first: the first
+    solves of each plan size in a process pay one-off costs (growing the
+    stream-ordered memory pool, first launches of each kernel) that a
+    running server has paid."""
     from paper_1205_4139_gb300 import binding
     reqs = synth.serving_requests(n_req, rate=rate, seed=0)
     ctx = mp.get_context("spawn")
@@ -539,7 +540,8 @@ def serving(n_req: int, rate: float = 2000.0, workers: int = 8, budget_gb: float
         data = pool.map(_serving_gen, reqs)
     q = lambda v, f: v[min(len(v) - 1, int(f * (len(v) - 1) + 0.5))]
 
-    def replay(scale):
+    def replay(scale, n=None):
+        n = len(reqs) if n is None else n
         srv = binding.Server(workers=workers, budget_bytes=int(budget_gb * (1 << 30)))
         for kind in ("wht", "dft"):  # warm-up: one small job per kind
             w = synth.serving_requests(1, seed=99, log_n_lo=14, log_n_hi=14, k_lo=32, k_hi=32)[0]
@@ -548,7 +550,7 @@ def serving(n_req: int, rate: float = 2000.0, workers: int = 8, budget_gb: float
             srv.submit(kind, "fp32", w["N"], om, yv, w["K"])
         srv.wait_all()
         t0 = time.perf_counter()
-        for r, (om, yv) in zip(reqs, data):
+        for r, (om, yv) in zip(reqs[:n], data[:n]):
             dt = r["arrival_s"] * scale - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
@@ -558,17 +560,17 @@ def serving(n_req: int, rate: float = 2000.0, workers: int = 8, budget_gb: float
         lat = sorted((r["t_done_us"] - r["t_submit_us"]) * 1e-3 for r in res)
         wait = sorted((r["t_admit_us"] - r["t_submit_us"]) * 1e-3 for r in res)
         span = (max(r["t_done_us"] for r in res) - min(r["t_submit_us"] for r in res)) * 1e-6
-        offered = len(res) / (reqs[-1]["arrival_s"] * scale) if scale > 0 else None
+        offered = len(res) / (reqs[n - 1]["arrival_s"] * scale) if scale > 0 else None
         return {"offered_per_s": offered, "requests": len(res),
                 "failed": sum(1 for r in res if r["status"] != 0 or r["device_error"] != 0),
                 "solves_per_s": len(res) / span, "latency_ms_p50": q(lat, 0.5), "latency_ms_p99": q(lat, 0.99),
                 "queue_wait_ms_p50": q(wait, 0.5), "makespan_s": span}
 
-    replay(0.0)  # warm-up: every request at once, untimed
+    replay(0.0, min(len(reqs), 160))  # warm-up: the first requests at once, untimed
     sat = replay(1.0)
     sus = replay(rate / max(1e-9, 0.5 * sat["solves_per_s"]))
     return {"workload": f"{n_req} requests, Poisson, N=2^14..2^20, M=N/8, K=32..1024, WHT/DFT fp32, "
-                        "OMP or CoSaMP (CoSaMP K capped at 128)",
+                        "OMP or CoSaMP (CoSaMP K capped at M/3)",
             "workers": workers, "budget_gb": budget_gb, "at_offered_rate": sat, "at_half_saturation": sus}
 
 
@@ -790,7 +792,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests in the serving measurement")
     ap.add_argument("--uneven-instances", type=int, default=4096, help="instances of the uneven-batch measurement")
     ap.add_argument("--huge", action="store_true",
                     help="run only the one partial-DFT instance N=2^22, M=2^19, K=4096, 30 dB")

@@ -342,7 +342,7 @@ cs_status cs_omp_noalloc(cs_plan_t plan, const void* y_dev, int64_t batch, int32
  * Runs cs_omp with CS_PATH_HYBRID on the caller's batch (y_dev, batch, K,
  * rel_tol) at a ladder of switch points: 1 (transforms from t = 2 on), the
  * flop-model point, 8, 12, 16, 24, 36, ... and K (kernel sums throughout);
- * each is timed with CUDA events on `stream` (one warm-up, best of three).
+ * each is timed with CUDA events on `stream` (in rounds over the whole ladder: one warm-up round, then the best of five).
  * The fastest becomes the plan's switch point for calls that pass
  * t_switch < 0, and is written to *t_best.  If cap > 0, the first
  * min(cap, n) ladder entries and their times in ms go to cand_out (int32) and

@@ -1015,10 +1015,12 @@ extern "C" cs_status cs_plan_tune(cs_plan_t plan, const void* y_dev, int64_t bat
       rc = cuda_fail(e, "tune events");
       break;
     }
-    for (size_t i = 0; i < ladder.size() && rc == CS_OK; ++i) {
-      const cs_halt h = {rel_tol, CS_PATH_HYBRID, ladder[i], 0};
-      float best = 0.0f;
-      for (int rep = 0; rep < 4 && rc == CS_OK; ++rep) {  // one warm-up, best of three
+    // rounds over the whole ladder (one warm-up round, then the best of
+    // five per candidate), so that a slow drift of the clocks or of the
+    // memory state during the sweep weighs on every candidate alike
+    for (int rep = 0; rep < 6 && rc == CS_OK; ++rep) {
+      for (size_t i = 0; i < ladder.size() && rc == CS_OK; ++i) {
+        const cs_halt h = {rel_tol, CS_PATH_HYBRID, ladder[i], 0};
         if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { rc = cuda_fail(e, "tune record"); break; }
         rc = cs_omp(plan, y_dev, batch, K, &h, x, supp, nullptr, nullptr, stream);
         if (rc != CS_OK) break;
@@ -1028,9 +1030,8 @@ extern "C" cs_status cs_plan_tune(cs_plan_t plan, const void* y_dev, int64_t bat
         }
         float t = 0.0f;
         cudaEventElapsedTime(&t, e0, e1);
-        if (rep == 1 || (rep > 1 && t < best)) best = t;
+        if (rep == 1 || (rep > 1 && t < ms[i])) ms[i] = t;
       }
-      ms[i] = best;
     }
   } while (0);
   if (e0) cudaEventDestroy(e0);

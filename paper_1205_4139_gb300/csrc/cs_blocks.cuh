@@ -244,6 +244,52 @@ __device__ int correlate_residual(const Grp& g, E* buf, const PlanDev<E>& P, con
   return group_argmax(g, sk.bv, sk.bj, rv, rj);
 }
 
+// residual_on_omega with the norm chosen at run time (one inlined copy of
+// the forward transform where a caller needs both forms).
+template <class E, bool DFT>
+__device__ double residual_on_omega_rt(const Grp& g, E* buf, const PlanDev<E>& P, const E* __restrict__ y,
+                                       const uint32_t* bits, const uint16_t* kidx, const E* xw, double* red,
+                                       bool norm) {
+  using R = typename FT<E>::R;
+  const int N = P.N;
+  const SparseLoader<E> sl{bits, kidx, xw};
+  if constexpr (DFT) dft_forward(g, buf, P.logN, P.tw, sl, NoSink{});
+  else wht(g, buf, P.logN, sl, NoSink{});
+  const R sy = inv_sqrt_pow2<R>(P.logN), sx = (R)1 / (R)N;
+  if (norm) {  // two loops: no FP64 instruction, even predicated off, in the plain one
+    double acc[1] = {0.0};
+    for (int pos = g.tid; pos < N; pos += g.n) {
+      const int m = __ldg(P.slot + pos);
+      const int a = swz<E>(pos);
+      const E r = m >= 0 ? sub(scale(y[m], sy), scale(buf[a], sx)) : zero<E>();
+      acc[0] += norm2(to_w(r));
+      buf[a] = r;
+    }
+    group_sum(g, acc, red);  // ends with a group barrier
+    return acc[0] * (double)N;
+  }
+  for (int pos = g.tid; pos < N; pos += g.n) {
+    const int m = __ldg(P.slot + pos);
+    const int a = swz<E>(pos);
+    buf[a] = m >= 0 ? sub(scale(y[m], sy), scale(buf[a], sx)) : zero<E>();
+  }
+  g.sync();
+  return 0.0;
+}
+
+// The second half of correlate_residual for OMP: the adjoint transform of
+// the residual on the buffer, its last pass feeding the arg-max over j not
+// in Lambda (bits).  Returns the arg-max to every thread of g.
+template <class E, bool DFT>
+__device__ int adjoint_argmax(const Grp& g, E* buf, const PlanDev<E>& P, const uint32_t* bits,
+                              typename NormT<E>::V* rv, int* rj) {
+  using V = typename NormT<E>::V;
+  ArgmaxSink<E> sk{bits, nullptr, (V)-1, 0x7fffffff, nullptr};
+  if constexpr (DFT) dft_adjoint(g, buf, P.logN, P.tw, NoLoad{}, sk);
+  else wht(g, buf, P.logN, NoLoad{}, sk);
+  return group_argmax(g, sk.bv, sk.bj, rv, rj);
+}
+
 // Explicit residual check of the halting test (step 8) in FP32 mode.  The
 // FP64 downdate ||r_t||^2 = ||y||^2 - sum |zeta_k|^2 carries the FP32
 // rounding of h_0 on its right-hand side (about 1e-7 ||y||^2), so it cannot

@@ -189,29 +189,31 @@ __device__ void corr_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const
   const int p = S.p, t = p + 1;
   const bool fast = a.path == PATH_FAST || (a.path == PATH_HYBRID && t <= a.t_switch);
   int l;
-  if (S.chk) {  // halting test of step 8 on the explicit residual (FP32 mode)
-    const bool last = p >= a.K;
-    double r2;
-    if (!last && !fast) {  // the transform path forms the residual anyway
-      l = correlate_residual<E, DFT, true>(g, regA, a.P, a.y + S.b * M, v.bits, v.kidx, v.xw, rv, rj, nullptr,
-                                           nullptr, &r2, red);
-    } else {
-      r2 = residual_on_omega<E, DFT, true>(g, regA, a.P, a.y + S.b * M, v.bits, v.kidx, v.xw, red);
-    }
+  // The residual y - Phi x is formed by the transform path's correlation,
+  // and for the halting test of step 8 on the explicit residual (FP32 mode,
+  // S.chk); one call site each for the residual, the adjoint transform and
+  // the kernel sums keeps the kernel within its register budget.
+  constexpr bool kChk = sizeof(typename FT<E>::R) == 4;  // FP64 mode never sets S.chk
+  if ((kChk && S.chk) || !fast) {
+    const bool chk = kChk && S.chk;
+    const double r2 = residual_on_omega_rt<E, DFT>(g, regA, a.P, a.y + S.b * M, v.bits, v.kidx, v.xw, red, chk);
     if (g.tid == 0) c_valid = 0;
-    const double ynorm2 = S.ynorm2;
-    if (last || r2 < a.rel_tol * a.rel_tol * ynorm2) {
-      write_outputs(g, a, v, S.b, p, ynorm2, r2);
-      g.sync();
-      if (g.tid == 0) S.state = NEED_INIT;
-      return;
-    }
-    g.sync();  // every thread has read S before it changes
-    if (g.tid == 0) {
-      S.rn2 = r2;
-      S.chk = 0;
+    if (chk) {
+      const double ynorm2 = S.ynorm2;
+      if (p >= a.K || r2 < a.rel_tol * a.rel_tol * ynorm2) {
+        write_outputs(g, a, v, S.b, p, ynorm2, r2);
+        g.sync();
+        if (g.tid == 0) S.state = NEED_INIT;
+        return;
+      }
+      g.sync();  // every thread has read S before it changes
+      if (g.tid == 0) {
+        S.rn2 = r2;
+        S.chk = 0;
+      }
     }
     if (!fast) {
+      l = adjoint_argmax<E, DFT>(g, regA, a.P, v.bits, rv, rj);
       if (g.tid == 0) {
         S.lnew = l;
         S.state = NEED_LS;
@@ -219,16 +221,11 @@ __device__ void corr_step(const Grp& g, const OmpArgs<E>& a, SlotState& S, const
       return;
     }
   }
-  if (fast) {
-    if (!c_valid) {
-      load_kernel_vector<E, DFT>(g, regA, a.P, dbl);
-      if (g.tid == 0) c_valid = 1;
-    }
-    l = correlate_fast<E, DFT>(g, regA, v.h0, v.lam, v.xw, p, N, v.bits, nullptr, rv, rj, dbl);
-  } else {
-    l = correlate_residual<E, DFT>(g, regA, a.P, a.y + S.b * M, v.bits, v.kidx, v.xw, rv, rj);
-    if (g.tid == 0) c_valid = 0;
+  if (!c_valid) {
+    load_kernel_vector<E, DFT>(g, regA, a.P, dbl);
+    if (g.tid == 0) c_valid = 1;
   }
+  l = correlate_fast<E, DFT>(g, regA, v.h0, v.lam, v.xw, p, N, v.bits, nullptr, rv, rj, dbl);
   if (g.tid == 0) {
     S.lnew = l;
     S.state = NEED_LS;

@@ -19,6 +19,8 @@ numpy's PCG64 ``default_rng(seed)``.
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 WHT = "wht"
@@ -59,9 +61,24 @@ def sensing_column(kind: str, N: int, omega: np.ndarray, k: int) -> np.ndarray:
     return np.exp(-2j * np.pi * ph / N) / np.sqrt(N)
 
 
+@functools.lru_cache(maxsize=8)
+def _dft_entries(N: int) -> np.ndarray:
+    """exp(-2 pi i p / N) / sqrt(N) for p = 0 .. N-1: the values the entries
+    of A take (entry (i, k) is the one at p = i k mod N), each evaluated by
+    the same expression as in sensing_column."""
+    return np.exp(-2j * np.pi * np.arange(N, dtype=np.int64) / N) / np.sqrt(N)
+
+
 def measure(kind: str, N: int, omega: np.ndarray, support: np.ndarray, values: np.ndarray) -> np.ndarray:
     """Noiseless y = Phi x for x supported on ``support`` (FP64 / complex128)."""
     y = np.zeros(len(omega), dtype=np.complex128 if kind == DFT else np.float64)
+    if kind == DFT and len(support) > 8:
+        # the same column values, looked up instead of re-evaluated per column
+        om = omega.astype(np.int64)
+        w = _dft_entries(N)
+        for k, v in zip(support.tolist(), values.tolist()):
+            y += v * w[(om * np.int64(k)) % N]
+        return y
     for k, v in zip(support.tolist(), values.tolist()):
         y += v * sensing_column(kind, N, omega, k)
     return y
@@ -124,10 +141,11 @@ CONFIG_DFT_C64_BATCH = dict(kind=DFT, N=4096, M=1024, K=64, B=1024, snr_db=40.0,
 # Request stream of the serving workload: Poisson arrivals at `rate` per
 # second; N = 2^e with e uniform over [log_n_lo, log_n_hi]; M = N / 8; K
 # uniform over [k_lo, k_hi]; kind by a fair coin; OMP or CoSaMP by a fair
-# coin, CoSaMP's K capped at cosamp_k_max; noiseless Gaussian nonzeros; each
-# request has its own Omega and seed.
+# coin, CoSaMP's K capped at M/3 (its least squares run on up to 3K of the M
+# rows) and at cosamp_k_max; noiseless Gaussian nonzeros; each request has
+# its own Omega and seed.
 def serving_requests(n: int, rate: float = 2000.0, seed: int = 0, log_n_lo: int = 14, log_n_hi: int = 20,
-                     k_lo: int = 32, k_hi: int = 1024, cosamp_k_max: int = 128) -> list[dict]:
+                     k_lo: int = 32, k_hi: int = 1024, cosamp_k_max: int = 1024) -> list[dict]:
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=n))
     out = []
