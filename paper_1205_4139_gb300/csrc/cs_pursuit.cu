@@ -17,6 +17,7 @@
 // both also stop when ||r|| < rel_tol ||y|| or after max_iter iterations.
 // Least squares on a column set appends its columns, in ascending order, to
 // an empty FP64 inverse Cholesky factor (cs_ls.cuh).
+#include "cs_cg.cuh"
 #include "cs_internal.h"
 #include "cs_ls.cuh"
 #include "cs_select.cuh"
@@ -47,6 +48,10 @@ struct PursuitArgs {
 };
 
 __host__ __device__ inline int pursuit_mmax(int K, int algo) { return algo == ALGO_SP ? 2 * K : 3 * K; }
+// Column sets larger than this are solved by conjugate gradients (cs_cg.cuh,
+// a cluster of one CTA) instead of appending the columns to a factor.
+constexpr int kPCgMin = 96;
+__host__ __device__ inline bool pursuit_cg(int K, int algo) { return pursuit_mmax(K, algo) > kPCgMin; }
 
 template <class E>
 struct PLayout {
@@ -75,7 +80,11 @@ __host__ __device__ inline PLayout<E> pursuit_layout(int N, int K, int algo, int
   L.z = o;    o = a16(o + (size_t)mm * sizeof(W));
   L.x = o;    o = a16(o + (size_t)mm * sizeof(W));
   L.g = o;    o = a16(o + (size_t)mm * sizeof(W));
-  L.part = o; o = a16(o + (size_t)npart * sizeof(W) + (size_t)3 * mm * sizeof(double));
+  {  // the append's partial sums, or the conjugate-gradient scratch
+    const size_t part = (size_t)npart * sizeof(W) + (size_t)3 * mm * sizeof(double);
+    const size_t cgs = cg_smem_bytes<W>(mm, 1);
+    L.part = o; o = a16(o + (pursuit_cg(Kc, algo) && cgs > part ? cgs : part));
+  }
   L.lam = o;  o = a16(o + (size_t)mm * sizeof(int));
   L.sk = o;   o = a16(o + (size_t)mm * sizeof(unsigned long long));
   L.hist = o; o = a16(o + 258 * sizeof(int));
@@ -157,6 +166,28 @@ __global__ void __launch_bounds__(kPThreads) pursuit_kernel(PursuitArgs<E> a) {
   E* h0 = a.h0_ws + (size_t)blockIdx.x * N;
   const double tol2 = a.rel_tol * a.rel_tol;
   const int nbits = (N + 31) >> 5;
+  // Large column sets: least squares on cols[0..m) (ascending) by conjugate
+  // gradients from lv.x (warm) or zero, right-hand side h_0(cols); results
+  // in the append's places (lv.lam, lv.x, st.m, st.ls_rn2).  The scratch
+  // takes the append's partial-sum region, the right-hand side its z.
+  const bool cgm = pursuit_cg(K > 0 ? K : 1, a.algo);
+  cgx::cluster_group cl = cgx::this_cluster();  // a cluster of this one CTA
+  auto ls_cg = [&](const int* cols, int m, bool warm) {
+    W* rhs = lv.z;
+    for (int i = g.tid; i < m; i += g.n) {
+      lv.lam[i] = cols[i];
+      rhs[i] = to_w(h0[cols[i]]);
+    }
+    g.sync();
+    const int max_it = 2 * m < 64 ? 64 : (2 * m > 4000 ? 4000 : 2 * m);
+    const CgResult r = cg_cluster<E, 1>(cl, a.P, lv.lam, m, rhs, warm ? lv.x : nullptr, lv.x, 1, 1e-12, max_it,
+                                        (unsigned char*)lv.part, mm);
+    if (g.tid == 0) {
+      st.m = m;
+      st.ls_rn2 = st.ynorm2 - r.bh;
+    }
+    g.sync();
+  };
 
   for (;;) {
     if (g.tid == 0) s_inst = atomicAdd(a.counter, 1);
@@ -181,7 +212,8 @@ __global__ void __launch_bounds__(kPThreads) pursuit_kernel(PursuitArgs<E> a) {
         for (int j = g.tid; j < N; j += g.n) keys[j] = sel_key((V)norm2(h0[j]));
         g.sync();
         group_topk(g, keys, N, K, S, hist, scr);
-        ls_set(g, a.P, lv, h0, S, K, st, sh);
+        if (cgm) ls_cg(S, K, false);
+        else ls_set(g, a.P, lv, h0, S, K, st, sh);
         for (int k = g.tid; k < st.m; k += g.n) { S[k] = lv.lam[k]; xs[k] = lv.x[k]; }
         if (g.tid == 0) { st.ns = st.m; st.rn2 = st.ls_rn2; }
         g.sync();
@@ -232,7 +264,16 @@ __global__ void __launch_bounds__(kPThreads) pursuit_kernel(PursuitArgs<E> a) {
         }
         g.sync();
         m = st.m;
-        ls_set(g, a.P, lv, h0, T, m, st, sh);          // b = LS on T (lv.lam, lv.x)
+        if (cgm) {  // b = LS on T from the support's coefficients (zero on the new columns)
+          for (int i = g.tid; i < m; i += g.n) {
+            const int j = T[i];
+            lv.x[i] = in_bits(bits, j) ? xs[kidx[j]] : W{};
+          }
+          g.sync();
+          ls_cg(T, m, true);
+        } else {
+          ls_set(g, a.P, lv, h0, T, m, st, sh);          // b = LS on T (lv.lam, lv.x)
+        }
         m = st.m;
         // prune: the K entries of b with the largest |b| (ties to the lower column)
         for (int i = g.tid; i < m; i += g.n) sk[i] = sel_key(norm2(lv.x[i]));
@@ -259,7 +300,15 @@ __global__ void __launch_bounds__(kPThreads) pursuit_kernel(PursuitArgs<E> a) {
             if (g.tid == 0) st.rn2_new = st.rn2;
             g.sync();
           } else {
-            ls_set(g, a.P, lv, h0, T, kk, st, sh);        // x_new = LS on T_new
+            if (cgm) {  // x_new = LS on T_new from b's values there
+              for (int i = g.tid; i < kk; i += g.n) lv.g[i] = lv.x[sel[i]];
+              g.sync();
+              for (int i = g.tid; i < kk; i += g.n) lv.x[i] = lv.g[i];
+              g.sync();
+              ls_cg(T, kk, true);
+            } else {
+              ls_set(g, a.P, lv, h0, T, kk, st, sh);        // x_new = LS on T_new
+            }
             if (g.tid == 0) st.rn2_new = st.ls_rn2;
             g.sync();
           }
@@ -369,7 +418,8 @@ int pursuit_grid(const PlanView& P, int K, int algo, int fast, int64_t batch, in
 
 size_t pursuit_workspace_bytes(const PlanView& P, int K, int algo, int grid) {
   const size_t mm = (size_t)pursuit_mmax(K > 0 ? K : 1, algo);
-  return 16 + a16((size_t)grid * P.N * pes(P)) + a16((size_t)grid * (mm * (mm + 1) / 2) * pws(P));
+  const size_t fac = pursuit_cg(K > 0 ? K : 1, algo) ? 0 : (mm * (mm + 1) / 2) * pws(P);
+  return 16 + a16((size_t)grid * P.N * pes(P)) + a16((size_t)grid * fac);
 }
 
 cudaError_t launch_pursuit(const PlanView& P, const PursuitLaunch& a, void* ws, int grid, cudaStream_t st) {

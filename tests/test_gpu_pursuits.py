@@ -69,3 +69,23 @@ def test_pursuit_rejects_sizes():
         plan.pursuit("sp", y, 17)       # 2K > M
     x, supp, iters, rn = plan.pursuit("sp", y, 4)   # zero measurement: no iteration
     assert int(iters[0]) == 0 and (supp.cpu().numpy() == -1).all()
+
+
+@pytest.mark.parametrize("kind,prec", MODES)
+@pytest.mark.parametrize("algo", ["sp", "cosamp"])
+@pytest.mark.parametrize("path", ["fast", "conv"])
+def test_pursuit_cg_noiseless(kind, prec, algo, path):
+    """K = 64 on one-CTA plans: column sets of 128 (SP) and 192 (CoSaMP)
+    take the conjugate-gradient least squares; supports, iteration counts
+    and coefficients as the oracle's (dense Cholesky solves)."""
+    inst = synth.make_batch(kind, 4096, 1024, 64, 2, snr_db=None, prec=prec, seed=43)
+    run_and_check(inst, algo, path, prec)
+
+
+@pytest.mark.parametrize("algo", ["sp", "cosamp"])
+def test_pursuit_cg_dft_c64_noisy(algo):
+    """The benchmark's SP workload shape (partial DFT complex64, N = 4096,
+    M = 1024, K = 64, 40 dB) against the oracle, least squares by conjugate
+    gradients."""
+    inst = synth.make_batch("dft", 4096, 1024, 64, 3, snr_db=40.0, prec="fp32", seed=7)
+    run_and_check(inst, algo, "fast", "fp32", noiseless=False)
