@@ -27,6 +27,8 @@ struct cs_plan_s {
   int* d_slot_chain = nullptr;  // 8192 < N <= 2^16, DFT: slot map in the one-CTA chains' order
   int* d_om_off = nullptr;      // large plans: Omega by pass-2 row (offsets)
   int2* d_om_ent = nullptr;     //   and entries (j, m)
+  int* d_oc_off = nullptr;      // large plans: Omega by pass-1 column (offsets)
+  int2* d_oc_ent = nullptr;     //   and entries (j, m)
   void* d_tw64 = nullptr;
   void* d_tw32 = nullptr;
   void* d_c64 = nullptr;
@@ -173,7 +175,7 @@ int batch_group(const csf::PlanView& v) { return (v.dft ? 4 : 0) + (v.fp32 ? 0 :
 
 static void plan_free(cs_plan_s* p) {
   if (!p) return;
-  void* bufs[] = {p->d_slot, p->d_slot_chain, p->d_om_off, p->d_om_ent, p->d_tw64, p->d_tw32,
+  void* bufs[] = {p->d_slot, p->d_slot_chain, p->d_om_off, p->d_om_ent, p->d_oc_off, p->d_oc_ent, p->d_tw64, p->d_tw32,
                   p->d_c64,  p->d_c32,        p->d_ci,     p->d_lt64,   p->d_lt32, p->d_status, p->ws};
   for (void* b : bufs) {
     if (!b) continue;
@@ -304,6 +306,30 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
     PLAN_TRY(cudaMemcpyAsync(p->d_om_ent, om_ent.data(), om_ent.size() * sizeof(int2), cudaMemcpyHostToDevice, st),
              "copy Omega rows");
   }
+  // and grouped by the pass-1 column it goes into (j mod N2, both kinds), so
+  // that pass 1 of a zero-filled input assembles its columns from Omega's
+  // entries alone instead of reading a slot for every position
+  std::vector<int32_t> oc_off;
+  std::vector<int2> oc_ent;
+  if (large && M > 0) {
+    const int N2 = 1 << p->v.n2;
+    oc_off.assign((size_t)N2 + 1, 0);
+    for (int64_t m = 0; m < M; ++m) ++oc_off[(size_t)(omega_host[m] & (N2 - 1)) + 1];
+    for (int c = 0; c < N2; ++c) oc_off[(size_t)c + 1] += oc_off[(size_t)c];
+    oc_ent.resize((size_t)M);
+    std::vector<int32_t> fill(oc_off.begin(), oc_off.end() - 1);
+    for (int64_t m = 0; m < M; ++m) {
+      const int j = omega_host[m];
+      oc_ent[(size_t)fill[(size_t)(j & (N2 - 1))]++] = make_int2(j, (int)m);
+    }
+    PLAN_TRY(plan_alloc(p, (void**)&p->d_oc_off, oc_off.size() * sizeof(int32_t)), "cudaMalloc Omega columns");
+    PLAN_TRY(cudaMemcpyAsync(p->d_oc_off, oc_off.data(), oc_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             st),
+             "copy Omega columns");
+    PLAN_TRY(plan_alloc(p, (void**)&p->d_oc_ent, oc_ent.size() * sizeof(int2)), "cudaMalloc Omega columns");
+    PLAN_TRY(cudaMemcpyAsync(p->d_oc_ent, oc_ent.data(), oc_ent.size() * sizeof(int2), cudaMemcpyHostToDevice, st),
+             "copy Omega columns");
+  }
   if (kind == CS_DFT && !large) {
     PLAN_TRY(plan_alloc(p, &p->d_tw64, (size_t)N * sizeof(double2)), "cudaMalloc twiddles");
     if (prec == CS_FP32) PLAN_TRY(plan_alloc(p, &p->d_tw32, (size_t)N * sizeof(float2)), "cudaMalloc twiddles");
@@ -332,6 +358,8 @@ static cs_status plan_create_impl(int64_t N, const int32_t* omega_host, int64_t 
   p->v.ci = p->d_ci;
   p->v.om_off = p->d_om_off;
   p->v.om_ent = p->d_om_ent;
+  p->v.oc_off = p->d_oc_off;
+  p->v.oc_ent = p->d_oc_ent;
   if (!large) {
     p->v.slot_chain = p->d_slot;
     p->v.ctw64 = p->d_tw64;
@@ -430,6 +458,7 @@ size_t solve_footprint(int64_t N, int64_t M, int32_t kind, int32_t prec, int32_t
   if (v.large) b += (size_t)N * wb;  // kernel-vector scratch while the plan is built
   if (v.dft && v.large && logN <= kMaxLogNMulti) b += (size_t)N * 4;  // chain-order slot map
   if (v.large) b += ((size_t)1 << v.n1) * 4 + 4 + (size_t)M * 8;      // Omega grouped by pass-2 row
+  if (v.large) b += ((size_t)1 << v.n2) * 4 + 4 + (size_t)M * 8;      //   and by pass-1 column
   size_t ws = 0;
   if (algo == 0) ws = v.large ? large_omp_ws(v, K, CS_PATH_HYBRID, 1) : omp_workspace_bytes(v, K, 1);
   else if (v.large) ws = large_pursuit_ws(v, K, algo == 2 ? 0 : 1, 0, 1);

@@ -54,6 +54,10 @@ struct PlanView {
   // om_off[r + 1]) = (j, m) with j = Omega_m
   const int* om_off;
   const int2* om_ent;
+  // large plans: Omega grouped by the pass-1 column of the four-step view
+  // (j mod N2): entries oc_ent[oc_off[c] .. oc_off[c + 1]) = (j, m)
+  const int* oc_off;
+  const int2* oc_ent;
 };
 
 enum { CFMT_FULL = 0, CFMT_HALF = 1, CFMT_INT = 2 };

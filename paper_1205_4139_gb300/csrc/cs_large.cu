@@ -52,6 +52,8 @@ struct LDev {
   const int* __restrict__ slot;  // [N] natural order: m if j = Omega_m, else -1
   const int* __restrict__ om_off;   // Omega by pass-2 row: offsets [N1 + 1] (NULL if M = 0)
   const int2* __restrict__ om_ent;  //   entries (j, m), grouped by row
+  const int* __restrict__ oc_off;   // Omega by pass-1 column: offsets [N2 + 1] (NULL if M = 0)
+  const int2* __restrict__ oc_ent;  //   entries (j, m), grouped by column
   const E* __restrict__ tw1;     // DIF twiddles of the N1 chain
   const E* __restrict__ tw2;     // DIF twiddles of the N2 chain
   const E* __restrict__ wlo;     // w_N^m, m < 2^wsh
@@ -74,6 +76,8 @@ LDev<E> ldev(const PlanView& P) {
   d.slot = P.slot;
   d.om_off = P.om_off;
   d.om_ent = P.om_ent;
+  d.oc_off = P.oc_off;
+  d.oc_ent = P.oc_ent;
   constexpr bool f32 = sizeof(typename FT<E>::R) == 4;
   const E* t = (const E*)(f32 ? P.lt32 : P.lt64);
   const int N1 = 1 << P.n1, N2 = 1 << P.n2;
@@ -211,9 +215,11 @@ __device__ __forceinline__ void build_position_table(short* tab, int lg) {
 // ----------------------------------------------------------------- pass 1
 // out[b][k1 N2 + i2] = (w_N^(i2 k1) for DFT) * sum_i1 v(i2 + N2 i1) w_N1^(i1 k1)
 // for the C columns i2 of this CTA, v = in (LD_DENSE, stride in_stride),
-// zf_Omega(in) (LD_ZF, in has M entries per instance) or zf_Omega(1)
-// (LD_ONES).  Only the forward transform F is computed here: the adjoint is
-// read off it by index negation in pass 2.
+// zf_Omega(in) (LD_ZF, in has in_stride >= M entries per instance, indexed
+// by m: the tile is cleared and Omega's entries in its columns placed, read
+// from the plan's grouping of Omega by column) or zf_Omega(1) (LD_ONES).
+// Only the forward transform F is computed here: the adjoint is read off it
+// by index negation in pass 2.
 template <class E, bool DFT, int LD>
 __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restrict__ in, int64_t in_stride,
                                                    E* __restrict__ out, const LState* __restrict__ st) {
@@ -233,7 +239,27 @@ __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restric
   if constexpr (LD == LD_DENSE) {
     for (int q = threadIdx.x; q < tot; q += kLT)
       cp_async_elem(buf + (q & (C - 1)) * cs + swz<E>(q >> LC), src + c0 + (q & (C - 1)) + ((q >> LC) << n2));
-  } else {  // zero-filled gathers through the slot map, kU in flight per thread
+  } else if constexpr (LD == LD_ZF) {
+    // clear the C buffers (C * cs * sizeof(E) is a multiple of 16 bytes)
+    uint4* z4 = (uint4*)buf;
+    const int n4 = (int)(((size_t)C * cs * sizeof(E)) >> 4);
+    for (int q = threadIdx.x; q < n4; q += kLT) z4[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    if (P.oc_off) {  // Omega's entries in columns c0 .. c0 + C - 1, kU in flight per thread
+      const int e0 = __ldg(P.oc_off + c0), e1 = __ldg(P.oc_off + c0 + C), msk = (1 << n2) - 1;
+      for (int q0 = e0 + (int)threadIdx.x; q0 < e1; q0 += kU * kLT) {
+        int2 jm[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) jm[u] = q0 + u * kLT < e1 ? __ldg(P.oc_ent + q0 + u * kLT) : make_int2(-1, 0);
+        E v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) v[u] = jm[u].x >= 0 ? src[jm[u].y] : zero<E>();
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          if (jm[u].x >= 0) buf[((jm[u].x & msk) - c0) * cs + swz<E>(jm[u].x >> n2)] = v[u];
+      }
+    }
+  } else {  // LD_ONES: zero-filled through the slot map, kU in flight per thread
     for (int q0 = threadIdx.x; q0 < tot; q0 += kU * kLT) {
       int m[kU];
 #pragma unroll
@@ -243,10 +269,7 @@ __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restric
       }
       E v[kU];
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        if constexpr (LD == LD_ZF) v[u] = m[u] >= 0 ? src[m[u]] : zero<E>();
-        else v[u] = m[u] >= 0 ? one_e<E>() : zero<E>();
-      }
+      for (int u = 0; u < kU; ++u) v[u] = m[u] >= 0 ? one_e<E>() : zero<E>();
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         const int q = q0 + u * kLT;
@@ -290,7 +313,8 @@ __global__ void __launch_bounds__(kLT) lcol_kernel(LDev<E> P, const E* __restric
 // v = scl * X is handed to the sink:
 //   SK_H    out[j] = v (if out), arg-max over all j      -> partial
 //   SK_ARG  arg-max over j whose bit is clear in `bits` -> partial
-//   SK_RES  out[j] = y[m] - v where j = Omega_m (other j untouched)
+//   SK_RES  out[m] = y[m] - v where j = Omega_m (the residual on Omega,
+//           compact: M entries per instance)
 //   SK_KV   out[j] = v
 //   SK_RESN only for instances whose state asks for the explicit residual:
 //           the CTA's FP64 share of sum |y[m] - v|^2 over Omega's members in
@@ -340,7 +364,7 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
   __syncthreads();
   tile_chain<E, DFT>(buf, n2, cs, P.tw2);
   __syncthreads();
-  E* dst = out ? out + b * (int64_t)P.N : nullptr;
+  E* dst = out ? out + b * (int64_t)(SK == SK_RES ? P.M : P.N) : nullptr;
   const E* yb = y ? y + b * (int64_t)P.M : nullptr;
   const uint32_t* bb = bits ? bits + b * (int64_t)(P.N >> 5) : nullptr;
   if constexpr (SK == SK_RESN) {  // ||y - Phi x||^2, this CTA's share, FP64, fixed order
@@ -382,7 +406,7 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
           c = (j >> n2) - r0;
           pos = j & (N2 - 1);
         }
-        dst[j] = sub(yb[jm.y], scale(buf[c * cs + swz<E>(pos)], scl));
+        dst[jm.y] = sub(yb[jm.y], scale(buf[c * cs + swz<E>(pos)], scl));
       }
       return;
     }
@@ -434,7 +458,7 @@ __global__ void __launch_bounds__(kLT) lrow_kernel(LDev<E> P, const E* __restric
           }
         }
       } else if constexpr (SK == SK_RES) {
-        if (aux[u] >= 0) dst[j] = sub(yv[u], o);
+        if (aux[u] >= 0) dst[aux[u]] = sub(yv[u], o);
       } else {
         dst[j] = o;
       }
@@ -1178,7 +1202,7 @@ LOmpWs<E> lomp_ws(const PlanView& Pv, int K, int path, int64_t batch) {
   L.st = o;   o = al16(o + (size_t)batch * sizeof(LState));
   L.h0 = o;   o = al16(o + Nv);
   L.T = o;    o = al16(o + Nv);
-  L.Z = o;    o = al16(o + (conv ? Nv : 0));
+  L.Z = o;    o = al16(o + (conv ? (size_t)batch * P.M * sizeof(E) : 0));  // the residual on Omega
   L.xz = o;
   L.bits = o; o = al16(o + (size_t)batch * (P.N >> 5) * sizeof(uint32_t));
   L.B = o;    o = al16(o + (size_t)batch * ((Kc * (Kc + 1)) / 2) * sizeof(W));
@@ -1264,14 +1288,12 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
   E* Tc = (E*)(w + L.Tc);
   double* rpart = (double*)(w + L.rp);
   const bool chk_mode = resid_check<E>(a.rel_tol) && a.K > 0;
-  const size_t Nv = (size_t)batch * P.N * sizeof(E);
   cudaError_t e;
   if ((e = cudaMemsetAsync(A.st, 0, (size_t)batch * sizeof(LState), s)) != cudaSuccess) return e;
   if (A.colmap &&
       (e = cudaMemsetAsync(A.colmap, 0xff, (size_t)batch * ((size_t)1 << P.n2) * sizeof(int), s)) != cudaSuccess)
     return e;
   if ((e = cudaMemsetAsync(A.bits, 0, (size_t)batch * (P.N >> 5) * sizeof(uint32_t), s)) != cudaSuccess) return e;
-  if (Z && (e = cudaMemsetAsync(Z, 0, Nv, s)) != cudaSuccess) return e;
   const size_t ls_smem = (size_t)(a.K > 0 ? a.K : 1) * sizeof(W);
   if ((e = allow_smem(lls_one_kernel<E>, ls_smem)) != cudaSuccess) return e;
   if ((e = allow_smem(lls_u_kernel<E>, ls_smem)) != cudaSuccess) return e;
@@ -1301,7 +1323,7 @@ cudaError_t omp_t(const PlanView& Pv, const OmpLaunch& a, void* ws, cudaStream_t
       if ((e = run_row<E, DFT, SK_RES>(P, nullptr, 0, isq, Z, A.y, nullptr, nullptr, nullptr, 0, A.st, batch, s,
                                        LSparse<E>{Tc, A.cols, L.kc})) != cudaSuccess)
         return e;
-      if ((e = run_col<E, DFT, LD_DENSE>(P, Z, P.N, T, A.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_col<E, DFT, LD_ZF>(P, Z, P.M, T, A.st, batch, s)) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_ARG>(P, T, DFT, isq, nullptr, nullptr, A.bits, A.part_v, A.part_j, L.nparts,
                                        A.st, batch, s)) != cudaSuccess)
         return e;
@@ -2011,7 +2033,7 @@ LPWs<E> lp_ws(const PlanView& Pv, int K, int algo, int fast, int64_t batch) {
   L.h0 = o;   o = al16(o + Nv);
   L.H = o;    o = al16(o + Nv);
   L.T = o;    o = al16(o + Nv);
-  L.Z = o;    o = al16(o + (fast ? 0 : Nv));
+  L.Z = o;    o = al16(o + (fast ? 0 : (size_t)batch * Pv.M * (Pv.dft ? 2 : 1) * (Pv.fp32 ? 4 : 8)));
   L.xz = o;   o = al16(o + (fast ? 0 : Nv));
   L.bits = o; o = al16(o + (size_t)batch * (N >> 5) * sizeof(uint32_t));
   L.S = o;    o = al16(o + (size_t)batch * K * sizeof(int));
@@ -2152,7 +2174,6 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
   if ((e = cudaMemsetAsync(a.bits, 0, (size_t)batch * (P.N >> 5) * sizeof(uint32_t), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.S, 0, (size_t)batch * q.K * sizeof(int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.xsw, 0, (size_t)batch * q.K * sizeof(E), s)) != cudaSuccess) return e;
-  if (Z && (e = cudaMemsetAsync(Z, 0, Nv, s)) != cudaSuccess) return e;
   if (a.xz && (e = cudaMemsetAsync(a.xz, 0, Nv, s)) != cudaSuccess) return e;
   const size_t tile_smem = al16((size_t)kSelTile * sizeof(U)) + al16((size_t)a.kmax * sizeof(int)) + 300 * sizeof(int);
   const size_t merge_smem = al16((size_t)a.kmax * sizeof(int)) + 300 * sizeof(int);
@@ -2216,7 +2237,7 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
       if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, a.y, nullptr, nullptr, nullptr, 0, a.st, batch, s)) !=
           cudaSuccess)
         return e;
-      if ((e = run_col<E, DFT, LD_DENSE>(P, Z, P.N, T, a.st, batch, s)) != cudaSuccess) return e;
+      if ((e = run_col<E, DFT, LD_ZF>(P, Z, P.M, T, a.st, batch, s)) != cudaSuccess) return e;
       if ((e = run_row<E, DFT, SK_H>(P, T, DFT, isq, H, nullptr, nullptr, nullptr, nullptr, 0, a.st, batch, s)) !=
           cudaSuccess)
         return e;
