@@ -12,6 +12,11 @@ cs_omp_batched calls (the second is the one to capture).
   python profile_case.py uneven dft big 304
   python profile_case.py wht_tc 16384 4096
 
+With `cosamp N K`, one CoSaMP solve on a partial-DFT complex64 instance
+(M = N/8, noiseless, its least squares by cluster conjugate gradients):
+
+  python profile_case.py cosamp 1048576 1024
+
 With `wht_tc`, two cs_correlate calls on `batch` residuals of a partial-WHT
 FP32 plan with N points and M = N/4 rows (the tensor-core Hadamard stages;
 the second call is the one to capture).
@@ -66,6 +71,18 @@ def main():
         torch.cuda.synchronize()
         assert plan.device_error() == 0
         print("ok")
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "cosamp":
+        # one CoSaMP solve on a partial-DFT complex64 instance with N points,
+        # M = N/8 rows, noiseless, K atoms (least squares by the cluster
+        # conjugate gradients of cs_cg.cuh)
+        N, K = int(sys.argv[2]), int(sys.argv[3])
+        inst = synth.make_batch("dft", N, N // 8, K, 1, snr_db=None, prec="fp32", seed=5)
+        plan = binding.Plan(N, inst["omega"], "dft", "fp32")
+        x, s, it, rn = plan.pursuit("cosamp", torch.from_numpy(inst["Y"]).cuda(), K, path="hybrid")
+        torch.cuda.synchronize()
+        assert plan.device_error() == 0
+        print("ok", int(it[0]))
         return
     B = int(sys.argv[1]) if len(sys.argv) > 1 else 456
     single = len(sys.argv) > 2 and sys.argv[2] == "single"
