@@ -1374,7 +1374,14 @@ cudaError_t kv_t(const PlanView& Pv, void* c64, void* tmp, cudaStream_t s) {
 // ascending j, so ties still go to the lower index), and the step: least
 // squares on the candidate set, pruning and the stop rules, one CTA per
 // instance, as in the one-CTA kernel.
-constexpr int kSelTile = kLT * 8;
+constexpr int kSelTile = kLT * 8;  // outputs per tile of the first stage, at least
+// Outputs per tile: at least 8 times the candidates a tile keeps, so that the
+// second stage (one CTA per instance) sees at most N/8 candidates.
+__host__ __device__ inline int lp_tile(int N, int kmax) {
+  int t = kSelTile;
+  while (t < 8 * kmax && t < N) t <<= 1;
+  return t < N ? t : N;
+}
 
 struct LPExtra {  // per instance, beside the LState done flag
   int ns, m, it, pad;
@@ -1406,7 +1413,7 @@ struct LPArgs {
   E* xsw;           // [batch][K] coefficients in the working precision, 0 past ns
   U* ckey;          // [batch][ntiles][kmax] tile candidates
   int* cj;
-  int ntiles, kmax;
+  int ntiles, kmax, tile;  // tile: outputs per first-stage tile (lp_tile)
   int* sel;         // [batch][kmax] selection, ascending
   W* B;             // [batch][mm(mm+1)/2]
   LState* st;       // done flags
@@ -1441,21 +1448,22 @@ __global__ void __launch_bounds__(kLT) lp_tile_kernel(LPArgs<E> a, const E* __re
   using V = typename NormT<E>::V;
   extern __shared__ __align__(16) unsigned char sm[];
   U* keys = (U*)sm;
-  int* out = (int*)(sm + al16((size_t)kSelTile * sizeof(U)));
+  const int tile = a.tile;
+  int* out = (int*)(sm + al16((size_t)tile * sizeof(U)));
   int* hist = out + al16((size_t)k * sizeof(int)) / sizeof(int);
   int* scr = hist + 260;
   const int64_t b = blockIdx.y;
   if (a.st[b].done) return;
-  const int N = a.P.N, j0 = blockIdx.x * kSelTile;
+  const int N = a.P.N, j0 = blockIdx.x * tile;
   const E* hb = src + b * (int64_t)N;
   const uint32_t* bb = a.bits + b * (int64_t)(N >> 5);
-  for (int i = threadIdx.x; i < kSelTile; i += kLT) {
+  for (int i = threadIdx.x; i < tile; i += kLT) {
     const int j = j0 + i;
     keys[i] = (excl && in_bits(bb, j)) ? (U)0 : sel_key((V)norm2(hb[j]));
   }
   const Grp g = whole_block();
   g.sync();
-  group_topk(g, keys, kSelTile, k, out, hist, scr);
+  group_topk(g, keys, tile, k, out, hist, scr);
   U* ck = a.ckey + (b * a.ntiles + blockIdx.x) * (int64_t)a.kmax;
   int* cjj = a.cj + (b * a.ntiles + blockIdx.x) * (int64_t)a.kmax;
   for (int i = threadIdx.x; i < k; i += kLT) {
@@ -2007,7 +2015,7 @@ __global__ void __launch_bounds__(kLT) widen_kernel(const E* __restrict__ in, in
 template <class E>
 struct LPWs {
   size_t st, ex, h0, H, T, Z, xz, bits, S, xs, xsw, ck, cj, sel, B, yp, Tq, rq, xq, h64, T64, y64, total;
-  int ntiles, kmax, nyp;
+  int ntiles, kmax, nyp, tile;
 };
 
 // Column sets larger than this take the conjugate-gradient least squares.
@@ -2021,8 +2029,9 @@ LPWs<E> lp_ws(const PlanView& Pv, int K, int algo, int fast, int64_t batch) {
   LPWs<E> L;
   const size_t N = (size_t)Pv.N, Nv = (size_t)batch * N * (Pv.dft ? 2 : 1) * (Pv.fp32 ? 4 : 8);
   const int mm = lp_mmax(K, algo);
-  L.ntiles = (int)(N / kSelTile);
   L.kmax = algo == 0 ? K : 2 * K;
+  L.tile = lp_tile((int)N, L.kmax);
+  L.ntiles = (int)(N / L.tile);
   {
     const int64_t g = ((int64_t)Pv.M + 2047) / 2048;
     L.nyp = (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
@@ -2152,6 +2161,7 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
   a.ckey = (U*)(w + L.ck);
   a.cj = (int*)(w + L.cj);
   a.ntiles = L.ntiles;
+  a.tile = L.tile;
   a.kmax = L.kmax;
   a.sel = (int*)(w + L.sel);
   a.B = (W*)(w + L.B);
@@ -2175,7 +2185,7 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
   if ((e = cudaMemsetAsync(a.S, 0, (size_t)batch * q.K * sizeof(int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.xsw, 0, (size_t)batch * q.K * sizeof(E), s)) != cudaSuccess) return e;
   if (a.xz && (e = cudaMemsetAsync(a.xz, 0, Nv, s)) != cudaSuccess) return e;
-  const size_t tile_smem = al16((size_t)kSelTile * sizeof(U)) + al16((size_t)a.kmax * sizeof(int)) + 300 * sizeof(int);
+  const size_t tile_smem = al16((size_t)a.tile * sizeof(U)) + al16((size_t)a.kmax * sizeof(int)) + 300 * sizeof(int);
   const size_t merge_smem = al16((size_t)a.kmax * sizeof(int)) + 300 * sizeof(int);
   const size_t step_smem = lp_uses_cg(q.K, q.algo) ? 0 : lp_layout<E>(q.K, q.algo).total;
   if ((e = allow_smem(lp_tile_kernel<E>, tile_smem)) != cudaSuccess) return e;
