@@ -300,7 +300,8 @@ cs_status cs_omp_batched_tune(const cs_plan_t* plans, int64_t count, const void*
  * K > 32) they solve the normal equations by FP64 conjugate gradients, one
  * thread-block cluster of 4 to 16 CTAs per instance, Gram products read off
  * the FP64 kernel vector, from the previous coefficients, to a relative
- * residual of 1e-12 (at most 2m iterations for m columns, 64 to 4000); a
+ * residual of 1e-12 (FP64 plans; 1e-10 for FP32 plans, whose data carry
+ * FP32 rounding) in at most 2m iterations for m columns (64 to 4000); a
  * column set whose columns are dependent is then solved only as far as
  * the iterations reach, instead of dropping the dependent column.
  * Limits: 1 <= K, 2K <= M (SP), 3K <= M (CoSaMP), K <= 128 for N <= 8192,

@@ -94,6 +94,14 @@ __host__ __device__ inline size_t cg_smem_bytes(int mmax, int G) {
   return a16((size_t)mmax * sizeof(W)) + a16((size_t)mmax * sizeof(int)) + 3 * a16(sl * sizeof(W));
 }
 
+// Relative residual at which the solver stops: 1e-12 for FP64 plans; 1e-10
+// for FP32 plans, whose data carry FP32 rounding (about 6e-8 relative) far
+// above what the extra iterations would resolve.
+template <class E>
+__host__ __device__ constexpr double cg_tol() {
+  return sizeof(typename FT<E>::R) == 4 ? 1e-10 : 1e-12;
+}
+
 struct CgResult {
   double bh;   // Re b^H rhs + Re b^H r: ||y||^2 - ||y - Phi_T b||^2 for the solution b
   double q;    // quadratic form v^H G v (mode 2)

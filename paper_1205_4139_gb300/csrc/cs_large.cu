@@ -26,6 +26,7 @@
 // transform) and then the least squares, all on the caller's stream; a
 // finished instance makes every later kernel of that instance return at
 // once.
+#include <atomic>
 #include <cmath>
 
 #include "cs_blocks.cuh"
@@ -1431,6 +1432,7 @@ struct LPArgs {
   // FP32 plans: h_0 = Phi^H y once more in FP64 ([batch][N]), the right-hand
   // sides of the least squares (NULL: h0 is already FP64)
   const W* h64;
+  int* ndone;  // instances finished so far (the device-side loop stops at batch)
 };
 
 // (Phi^H y)(j) in FP64 for the least squares
@@ -1531,6 +1533,7 @@ __device__ void lp_outputs(const LPArgs<E>& a, int64_t b, const LPExtra& X) {
     if (a.iters_out) a.iters_out[b] = X.it;
     if (a.res_out) a.res_out[b] = X.ynorm2 > 0.0 ? sqrt(fmax(X.rn2, 0.0) / X.ynorm2) : 0.0;
     a.st[b].done = 1;
+    atomicAdd(a.ndone, 1);
   }
 }
 
@@ -2014,7 +2017,7 @@ __global__ void __launch_bounds__(kLT) widen_kernel(const E* __restrict__ in, in
 
 template <class E>
 struct LPWs {
-  size_t st, ex, h0, H, T, Z, xz, bits, S, xs, xsw, ck, cj, sel, B, yp, Tq, rq, xq, h64, T64, y64, total;
+  size_t st, ex, h0, H, T, Z, xz, bits, S, xs, xsw, ck, cj, sel, B, yp, Tq, rq, xq, h64, T64, y64, ctr, total;
   int ntiles, kmax, nyp, tile;
 };
 
@@ -2061,8 +2064,85 @@ LPWs<E> lp_ws(const PlanView& Pv, int K, int algo, int fast, int64_t batch) {
   L.h64 = o;  o = al16(o + (h64 ? (size_t)batch * N * sizeof(W) : 0));
   L.T64 = o;  o = al16(o + (h64 ? (size_t)batch * N * sizeof(W) : 0));
   L.y64 = o;  o = al16(o + (h64 ? (size_t)batch * Pv.M * sizeof(W) : 0));
+  L.ctr = o;  o = al16(o + 2 * sizeof(int));  // instances done, loop iterations
   L.total = o;
   return L;
+}
+
+// ------------------------------------------------ device-side iteration loop
+// The iterations of a large-plan pursuit are the same kernels every time,
+// with all their state on the device, and most instances stop long before
+// max_iter.  Instead of queuing max_iter copies of them from the host, the
+// call runs one CUDA graph whose conditional while node repeats them: a
+// one-thread kernel at the end of each pass counts it and lets the loop go on
+// while an instance is unfinished and the count is below the limit, so the
+// loop ends on the device as soon as the last instance does.
+
+__global__ void loop_ctl_kernel(cudaGraphConditionalHandle h, int* ctr, const int* ndone, int64_t batch,
+                                int limit) {
+  const int it = ++*ctr;
+  cudaGraphSetConditional(h, (*ndone < batch && it < limit) ? 1u : 0u);
+}
+
+// body(stream) enqueues one iteration.  Returns cudaErrorNotSupported, with
+// nothing queued, when the graph cannot be built (the caller then queues the
+// iterations itself).
+template <class F>
+cudaError_t device_loop(cudaStream_t s, int* ctr, const int* ndone, int64_t batch, int limit, F&& body) {
+  if (limit <= 0) return cudaSuccess;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node;
+  bool capturing = false;
+  cudaError_t rc = cudaSuccess;
+  do {
+    if (e != cudaSuccess) { rc = cudaErrorNotSupported; break; }
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+      rc = cudaErrorNotSupported;
+      break;
+    }
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) { rc = cudaErrorNotSupported; break; }
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { rc = cudaErrorNotSupported; break; }
+    if (cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = cudaErrorNotSupported;
+      break;
+    }
+    capturing = true;
+    rc = body(cs);
+    if (rc == cudaSuccess) {
+      loop_ctl_kernel<<<1, 1, 0, cs>>>(h, ctr, ndone, batch, limit);
+      rc = cudaGetLastError();
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &captured);
+    capturing = false;
+    if (rc != cudaSuccess) break;
+    if (ee != cudaSuccess) { rc = ee; break; }
+    if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      rc = cudaErrorNotSupported;
+      break;
+    }
+    if ((rc = cudaMemsetAsync(ctr, 0, sizeof(int), s)) != cudaSuccess) break;
+    rc = cudaGraphLaunch(x, s);
+  } while (0);
+  if (capturing) {
+    cudaGraph_t captured = nullptr;
+    (void)cudaStreamEndCapture(cs, &captured);
+  }
+  if (x) cudaGraphExecDestroy(x);  // a launched graph is freed once it completes
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  return rc;
 }
 
 // Conjugate-gradient launches: one cluster of G CTAs per instance.  A CTA
@@ -2077,8 +2157,13 @@ cudaError_t lq_cg_launch(const LPArgs<E>& a, int64_t batch, cudaStream_t s, bool
   auto kern = lq_cg_kernel<E, G>;
   cudaError_t e = allow_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  if (G > 8 && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
-    return e;
+  // set once per process (the launches inside a device-side loop are
+  // captured into a graph after the first iteration has set it)
+  static std::atomic<bool> nonportable{false};
+  if (G > 8 && !nonportable.load()) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+    nonportable.store(true);
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(batch * G));
   cfg.blockDim = dim3(kLT);
@@ -2172,15 +2257,17 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
   a.rq = a.lq ? (W*)(w + L.rq) : nullptr;
   a.xq = a.lq ? (W*)(w + L.xq) : nullptr;
   a.h64 = (a.lq && sizeof(E) != sizeof(W)) ? (const W*)(w + L.h64) : nullptr;
+  a.ndone = (int*)(w + L.ctr);
   {
     const int mm = lp_mmax(q.K, q.algo);
     a.cg_max = 2 * mm < 64 ? 64 : (2 * mm > 4000 ? 4000 : 2 * mm);
-    a.cg_tol = 1e-12;
+    a.cg_tol = cg_tol<E>();
   }
   const size_t Nv = (size_t)batch * P.N * sizeof(E);
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.st, 0, (size_t)batch * sizeof(LState), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.ex, 0, (size_t)batch * sizeof(LPExtra), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.ndone, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.bits, 0, (size_t)batch * (P.N >> 5) * sizeof(uint32_t), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.S, 0, (size_t)batch * q.K * sizeof(int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.xsw, 0, (size_t)batch * q.K * sizeof(E), s)) != cudaSuccess) return e;
@@ -2237,39 +2324,52 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int kk = q.algo == 0 ? q.K : 2 * q.K;
-  for (int it = 0; it < q.max_iter; ++it) {
+  // one iteration on stream st
+  auto iteration = [&](cudaStream_t st) -> cudaError_t {
+    cudaError_t e;
     if (q.fast) {  // h = h_0 - sum over the support (zero-padded to K atoms)
-      if ((e = run_fast<E, DFT>(P, a.h0, a.S, a.xsw, q.K, q.K, nullptr, H, nullptr, nullptr, 0, a.st, batch, s)) !=
+      if ((e = run_fast<E, DFT>(P, a.h0, a.S, a.xsw, q.K, q.K, nullptr, H, nullptr, nullptr, 0, a.st, batch, st)) !=
           cudaSuccess)
         return e;
     } else {  // r = y - Phi x by a forward transform of zf(x), then h = A^H zf(r)
-      if ((e = run_col<E, DFT, LD_DENSE>(P, a.xz, P.N, T, a.st, batch, s)) != cudaSuccess) return e;
-      if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, a.y, nullptr, nullptr, nullptr, 0, a.st, batch, s)) !=
+      if ((e = run_col<E, DFT, LD_DENSE>(P, a.xz, P.N, T, a.st, batch, st)) != cudaSuccess) return e;
+      if ((e = run_row<E, DFT, SK_RES>(P, T, 0, isq, Z, a.y, nullptr, nullptr, nullptr, 0, a.st, batch, st)) !=
           cudaSuccess)
         return e;
-      if ((e = run_col<E, DFT, LD_ZF>(P, Z, P.M, T, a.st, batch, s)) != cudaSuccess) return e;
-      if ((e = run_row<E, DFT, SK_H>(P, T, DFT, isq, H, nullptr, nullptr, nullptr, nullptr, 0, a.st, batch, s)) !=
+      if ((e = run_col<E, DFT, LD_ZF>(P, Z, P.M, T, a.st, batch, st)) != cudaSuccess) return e;
+      if ((e = run_row<E, DFT, SK_H>(P, T, DFT, isq, H, nullptr, nullptr, nullptr, nullptr, 0, a.st, batch, st)) !=
           cudaSuccess)
         return e;
     }
-    lp_tile_kernel<E><<<tgrid, kLT, tile_smem, s>>>(a, H, kk, q.algo == 0);
-    lp_merge_kernel<E><<<(unsigned)batch, kLT, merge_smem, s>>>(a, kk);
+    lp_tile_kernel<E><<<tgrid, kLT, tile_smem, st>>>(a, H, kk, q.algo == 0);
+    lp_merge_kernel<E><<<(unsigned)batch, kLT, merge_smem, st>>>(a, kk);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.lq) {
       // every launch is checked at once: a kernel that failed to start
       // would leave the next one working on the previous step's state
-      lq_form_kernel<E><<<(unsigned)batch, kLT, 0, s>>>(a, 1);
+      lq_form_kernel<E><<<(unsigned)batch, kLT, 0, st>>>(a, 1);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      if ((e = lq_cg<E>(a, batch, G, s)) != cudaSuccess) return e;
-      lq_prune_kernel<E><<<(unsigned)batch, kLT, prune_smem, s>>>(a, 1);
+      if ((e = lq_cg<E>(a, batch, G, st)) != cudaSuccess) return e;
+      lq_prune_kernel<E><<<(unsigned)batch, kLT, prune_smem, st>>>(a, 1);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      if ((e = lq_cg<E>(a, batch, G, s)) != cudaSuccess) return e;
-      lq_accept_kernel<E><<<(unsigned)batch, kLT, 0, s>>>(a);
+      if ((e = lq_cg<E>(a, batch, G, st)) != cudaSuccess) return e;
+      lq_accept_kernel<E><<<(unsigned)batch, kLT, 0, st>>>(a);
     } else {
-      lp_step_kernel<E><<<(unsigned)batch, kLT, step_smem, s>>>(a, 1);
+      lp_step_kernel<E><<<(unsigned)batch, kLT, step_smem, st>>>(a, 1);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+    return cudaSuccess;
+  };
+  // the first iteration from the host (it also sets the kernels' attributes),
+  // the others in a device-side loop; the host queues them all where the
+  // graph cannot be built
+  if (q.max_iter < 1) return cudaSuccess;
+  if ((e = iteration(s)) != cudaSuccess) return e;
+  e = device_loop(s, a.ndone + 1, a.ndone, batch, q.max_iter - 1, iteration);
+  if (e != cudaErrorNotSupported) return e;
+  (void)cudaGetLastError();
+  for (int it = 1; it < q.max_iter; ++it)
+    if ((e = iteration(s)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kPThreads) pursuit_kernel(PursuitArgs<E> a) {
     }
     g.sync();
     const int max_it = 2 * m < 64 ? 64 : (2 * m > 4000 ? 4000 : 2 * m);
-    const CgResult r = cg_cluster<E, 1>(cl, a.P, lv.lam, m, rhs, warm ? lv.x : nullptr, lv.x, 1, 1e-12, max_it,
+    const CgResult r = cg_cluster<E, 1>(cl, a.P, lv.lam, m, rhs, warm ? lv.x : nullptr, lv.x, 1, cg_tol<E>(), max_it,
                                         (unsigned char*)lv.part, mm);
     if (g.tid == 0) {
       st.m = m;

@@ -17,6 +17,11 @@ With `cosamp N K`, one CoSaMP solve on a partial-DFT complex64 instance
 
   python profile_case.py cosamp 1048576 1024
 
+With `sp batch`, subspace pursuit (K = 64, kernel sums) on the first
+`batch` instances of the partial-DFT complex64 workload:
+
+  python profile_case.py sp 304
+
 With `wht_tc`, two cs_correlate calls on `batch` residuals of a partial-WHT
 FP32 plan with N points and M = N/4 rows (the tensor-core Hadamard stages;
 the second call is the one to capture).
@@ -83,6 +88,17 @@ def main():
         torch.cuda.synchronize()
         assert plan.device_error() == 0
         print("ok", int(it[0]))
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "sp":
+        # subspace pursuit (kernel sums) on the first `batch` instances of the
+        # partial-DFT complex64 workload, K = 64
+        cfg = dict(synth.CONFIG_DFT_C64_BATCH)
+        cfg["B"] = int(sys.argv[2])
+        inst = synth.make_batch(**cfg)
+        plan = binding.Plan(cfg["N"], inst["omega"], cfg["kind"], cfg["prec"])
+        x, s, it, rn = plan.pursuit("sp", torch.from_numpy(inst["Y"]).cuda(), cfg["K"], path="fast")
+        torch.cuda.synchronize()
+        print("ok", float(it.float().mean()))
         return
     B = int(sys.argv[1]) if len(sys.argv) > 1 else 456
     single = len(sys.argv) > 2 and sys.argv[2] == "single"
