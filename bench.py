@@ -329,9 +329,24 @@ def secondary(args, dev, plan, inst, stream, flush, refs=None):
         v = _events_ms(lambda: p3.pursuit_into("cosamp", y3, 4, x3, s3, t3, r3, path=path, max_iter=8), 20, 3,
                        stream, flush)
         per_it[path] = statistics.median(v) / max(1.0, float(t3.sum()))
+    # the correlation alone, per instance: kernel sums over the K = 4 atoms of
+    # an estimate, and one transform (the transform path runs two per
+    # iteration: the residual and the correlation)
+    h3 = torch.zeros(B3, 8192, dtype=torch.complex64, device=dev)
+    sp3 = torch.from_numpy(np.stack([np.sort(np.random.default_rng(b).choice(8192, 4, replace=False))
+                                     for b in range(B3)]).astype(np.int32)).to(dev)
+    xw3 = torch.ones(B3, 4, dtype=torch.complex64, device=dev)
+    corr = {"kernel_sums_s4": statistics.median(_events_ms(lambda: p3.correlate_fast(h3, sp3, xw3, want_h=False),
+                                                           20, 3, stream, flush)) / B3,
+            "one_transform": statistics.median(_events_ms(lambda: p3.correlate(y3, want_h=False), 20, 3, stream,
+                                                          flush)) / B3}
     out["cosamp_M64_N8192_K4"] = {"ms_per_instance_iteration": per_it,
                                   "fast_over_conv": per_it["fast"] / per_it["conv"],
-                                  "paper_flop_model": costmodel.cosamp_fast_ratio(8192, 4)}
+                                  "paper_flop_model": costmodel.cosamp_fast_ratio(8192, 4),
+                                  "correlation_ms_per_instance": corr,
+                                  "correlation_share_of_iteration": {
+                                      "fast": corr["kernel_sums_s4"] / per_it["fast"],
+                                      "conv": 2 * corr["one_transform"] / per_it["conv"]}}
     out["wht_fp32_correlate"] = {"N4096": wht_correlate(dev, stream),
                                  "N256": wht_correlate(dev, stream, N=256, M=64, B=1 << 20, tc_default=True)}
     out["large_dft_c64_N4194304_M524288"] = large_single(dev, stream, flush)

@@ -43,19 +43,58 @@ __device__ void group_topk(const Grp& g, const U* keys, int n, int k, int* out, 
   for (int shift = BITS - 8; shift >= 0; shift -= 8) {
     for (int i = g.tid; i < 256; i += g.n) hist[i] = 0;
     g.sync();
-    for (int j = g.tid; j < n; j += g.n) {
-      const U kk = keys[j];
-      if ((kk & mask) == prefix) atomicAdd(&hist[(int)((kk >> shift) & (U)255)], 1);
+    // counts, one atomic per distinct digit per warp: the keys' leading
+    // digits (the exponent bits of |h|^2) are nearly all alike, and one
+    // atomic per key would serialise on a few buckets
+    for (int base = g.tid & ~31; base < n; base += g.n) {
+      const int j = base + (g.tid & 31);
+      bool in = false;
+      int dg = 0;
+      if (j < n) {
+        const U kk = keys[j];
+        in = (kk & mask) == prefix;
+        dg = (int)((kk >> shift) & (U)255);
+      }
+      const unsigned act = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const unsigned peers = __match_any_sync(act, dg);
+        if ((peers & ((1u << (g.tid & 31)) - 1u)) == 0u) atomicAdd(&hist[dg], __popc(peers));
+      }
     }
     g.sync();
-    if (g.tid == 0) {
-      int cum = 0, b = 255;
-      for (; b > 0; --b) {
-        if (cum + hist[b] >= need) break;
-        cum += hist[b];
+    // the digit: the highest bucket b whose count with all higher buckets'
+    // reaches `need` (bucket 0 if none of 255 .. 1 does), and how many keys
+    // of it are still needed.  One warp: lane l holds buckets 255 - 8l down
+    // to 248 - 8l, a shuffle scan gives every lane the keys above its chunk,
+    // and the lane whose chunk crosses `need` walks its eight buckets.
+    if (g.warp() == 0) {
+      const int l = g.lane(), top = 255 - 8 * l;
+      int c[8], sum = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        c[i] = hist[top - i];
+        sum += c[i];
       }
-      hist[256] = b;
-      hist[257] = need - cum;
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (l >= o) incl += v;
+      }
+      const int excl = incl - sum;
+      if (excl < need && (incl >= need || l == 31)) {  // exactly one lane
+        int cum = excl, b = top - 7;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (top - i == 0 || cum + c[i] >= need) {
+            b = top - i;
+            break;
+          }
+          cum += c[i];
+        }
+        hist[256] = b;
+        hist[257] = need - cum;
+      }
     }
     g.sync();
     const int b = hist[256];
