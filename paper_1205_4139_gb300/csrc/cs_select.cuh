@@ -43,23 +43,9 @@ __device__ void group_topk(const Grp& g, const U* keys, int n, int k, int* out, 
   for (int shift = BITS - 8; shift >= 0; shift -= 8) {
     for (int i = g.tid; i < 256; i += g.n) hist[i] = 0;
     g.sync();
-    // counts, one atomic per distinct digit per warp: the keys' leading
-    // digits (the exponent bits of |h|^2) are nearly all alike, and one
-    // atomic per key would serialise on a few buckets
-    for (int base = g.tid & ~31; base < n; base += g.n) {
-      const int j = base + (g.tid & 31);
-      bool in = false;
-      int dg = 0;
-      if (j < n) {
-        const U kk = keys[j];
-        in = (kk & mask) == prefix;
-        dg = (int)((kk >> shift) & (U)255);
-      }
-      const unsigned act = __ballot_sync(0xffffffffu, in);
-      if (in) {
-        const unsigned peers = __match_any_sync(act, dg);
-        if ((peers & ((1u << (g.tid & 31)) - 1u)) == 0u) atomicAdd(&hist[dg], __popc(peers));
-      }
+    for (int j = g.tid; j < n; j += g.n) {
+      const U kk = keys[j];
+      if ((kk & mask) == prefix) atomicAdd(&hist[(int)((kk >> shift) & (U)255)], 1);
     }
     g.sync();
     // the digit: the highest bucket b whose count with all higher buckets'
