@@ -111,3 +111,24 @@ def test_cg_pursuit_limits():
     plan3 = binding.Plan(4096, small["omega"], "wht", "fp32")
     with pytest.raises(binding.CsError, match="beyond the kernels"):
         plan3.pursuit("sp", torch.from_numpy(small["Y"]).cuda(), 129)
+
+
+@pytest.mark.parametrize("N,M", [(4096, 512), (1 << 14, 2048)])
+def test_cg_dependent_columns_end(N, M):
+    """A WHT row set that is a linear subspace (Omega = {0 .. M-1}): columns
+    j and j' coincide whenever j ^ j' has no low bits, so CoSaMP's candidate
+    sets hold whole groups of equal columns and their Gram matrices are
+    singular.  The conjugate-gradient least squares must still end (its
+    iteration bound), with finite outputs and a clean status word, on both
+    plan sizes."""
+    rng = np.random.default_rng(4)
+    omega = np.arange(M, dtype=np.int32)
+    K = 40
+    sup = np.sort(rng.choice(N, K, replace=False))
+    y = synth.measure("wht", N, omega, sup, rng.standard_normal(K))[None].astype(np.float64)
+    plan = binding.Plan(N, omega, "wht", "fp64")
+    x, supp, it, rn = plan.pursuit("cosamp", torch.from_numpy(y).cuda(), K, max_iter=6)
+    torch.cuda.synchronize()
+    assert np.isfinite(x.cpu().numpy()).all() and np.isfinite(float(rn[0]))
+    assert 1 <= int(it[0]) <= 6
+    assert plan.device_error() == 0
