@@ -2105,6 +2105,9 @@ LPWs<E> lp_ws(const PlanView& Pv, int K, int algo, int fast, int64_t batch) {
 // while an instance is unfinished and the count is below the limit, so the
 // loop ends on the device as soon as the last instance does.
 
+// Iterations after the first from which the device-side loop is used.
+constexpr int kDeviceLoopMin = 64;
+
 __global__ void loop_ctl_kernel(cudaGraphConditionalHandle h, int* ctr, const int* ndone, int64_t batch,
                                 int limit) {
   const int it = ++*ctr;
@@ -2388,13 +2391,19 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
     return cudaSuccess;
   };
   // the first iteration from the host (it also sets the kernels' attributes),
-  // the others in a device-side loop; the host queues them all where the
-  // graph cannot be built
+  // the others in a device-side loop when there are many of them to save
+  // (building and instantiating the graph costs host time on every call, and
+  // with many solves at once on several streams, as in the request runtime,
+  // the graphs slowed the whole mix: 65 -> 38 solves/s on the serving
+  // workload, where CoSaMP has max_iter 50); the host queues them where the
+  // graph is not worth it or cannot be built
   if (q.max_iter < 1) return cudaSuccess;
   if ((e = iteration(s)) != cudaSuccess) return e;
-  e = device_loop(s, a.ndone + 1, a.ndone, batch, q.max_iter - 1, iteration);
-  if (e != cudaErrorNotSupported) return e;
-  (void)cudaGetLastError();
+  if (q.max_iter - 1 >= kDeviceLoopMin) {
+    e = device_loop(s, a.ndone + 1, a.ndone, batch, q.max_iter - 1, iteration);
+    if (e != cudaErrorNotSupported) return e;
+    (void)cudaGetLastError();
+  }
   for (int it = 1; it < q.max_iter; ++it)
     if ((e = iteration(s)) != cudaSuccess) return e;
   return cudaSuccess;
