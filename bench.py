@@ -785,8 +785,12 @@ def run_gpu(args, rank: int, world: int, refs=None):
         "p50_ms": statistics.median(hs), "p99_ms": hs[min(len(hs) - 1, int(0.99 * len(hs)))],
         "correlations_per_s": corr, "plan_ms": plan_ms, "t_switch": best_ts, "t_switch_default": default_ts,
         "t_switch_sweep_ms": {str(k): round(v, 4) for k, v in tune.items()},
-        "fast": {"solves_per_s": B * world / (fast_med * 1e-3), "ms_per_step_p50": fast_med},
-        "conv": {"solves_per_s": B * world / (conv_med * 1e-3), "ms_per_step_p50": conv_med},
+        "fast": {"solves_per_s": B * world / (fast_med * 1e-3), "ms_per_step_p50": fast_med,
+                 "frac_of_fp32_peak": correlation_flops(N, it_np, best_ts, "fast") / (fast_med * 1e-3) / 1e12
+                 / fp32_measured},
+        "conv": {"solves_per_s": B * world / (conv_med * 1e-3), "ms_per_step_p50": conv_med,
+                 "frac_of_fp32_peak": correlation_flops(N, it_np, best_ts, "conv") / (conv_med * 1e-3) / 1e12
+                 / fp32_measured},
         "e2e": {"value": B * world / (e2e_mean * 1e-3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_measured, "unit": "TFLOP/s",
