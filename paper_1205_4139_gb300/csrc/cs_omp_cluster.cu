@@ -27,6 +27,7 @@ namespace {
 constexpr int kCL = 8;     // CTAs per instance (a portable cluster size)
 constexpr int kQT = 256;   // threads per CTA: the persistent kernel's correlation group
 constexpr int kQL = 128;   // the persistent kernel's least-squares group
+constexpr int kH0R = (1 << 13) / kCL / kQT;  // outputs of h per thread at N = 8192: 4
 enum { PATH_FAST = 0, PATH_CONV = 1, PATH_HYBRID = 2 };
 
 __host__ __device__ inline size_t q16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -145,6 +146,19 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kQT) omp_cluster_k
   }
   if (threadIdx.x == 0) rn2_s = ynorm2;
   __syncthreads();
+  // this CTA's slice of h_0 in registers (at most N / kCL / kQT = 4 outputs
+  // per thread for N <= 8192): the kernel sums of every iteration start from
+  // it without a global-memory round trip on their critical path
+  // (complex FP64 keeps reading the workspace: the 128-register budget has
+  // no room for it)
+  constexpr bool kRegH0 = sizeof(E) <= 8;
+  const int lo = (int)(((int64_t)N * r) / kCL), hi = (int)(((int64_t)N * (r + 1)) / kCL);
+  E h0r[kH0R];
+#pragma unroll
+  for (int i = 0; i < kH0R; ++i) {
+    const int j = lo + (int)threadIdx.x + i * kQT;
+    h0r[i] = (kRegH0 && j < hi) ? h0[j] : zero<E>();
+  }
   int p = 0, c_valid = 0;
   for (int it = 0;; ++it) {
     if (l < 0) {  // no candidate column left
@@ -196,12 +210,16 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kQT) omp_cluster_k
         c_valid = 1;
       }
       // this CTA's slice of h = h_0 - sum_k x_k c(j (-) lambda_k), same
-      // arithmetic per output as the persistent kernel
-      const int lo = (int)(((int64_t)N * r) / kCL), hi = (int)(((int64_t)N * (r + 1)) / kCL);
+      // arithmetic per output as the persistent kernel (the terms in k
+      // order; the unrolled loop only issues the next atoms' loads early)
       V bv = (V)-1;
       int bj = 0x7fffffff;
-      for (int j = lo + (int)threadIdx.x; j < hi; j += kQT) {
-        E acc = h0[j];
+#pragma unroll
+      for (int i = 0; i < kH0R; ++i) {
+        const int j = lo + (int)threadIdx.x + i * kQT;
+        if (j >= hi) break;
+        E acc = kRegH0 ? h0r[i] : h0[j];
+#pragma unroll 4
         for (int k = 0; k < p; ++k) {
           const int lk = lv.lam[k];
           const E xv = lv.xw[k];
