@@ -708,17 +708,27 @@ def run_gpu(args, rank: int, world: int, refs=None):
         return [e0.elapsed_time(e1) for e0, e1 in ev]
 
     # switch point: the flop-model default of Table I, and the one the
-    # library's tuner (cs_plan_tune) measures on this batch; the hybrid step
-    # then runs with t_switch = -1, i.e. the plan's tuned point
+    # library's tuner (cs_plan_tune) measures on this batch, checked below
+    # under the benchmark's own protocol
     default_ts = plan.info()["t_switch_default"]
     with ClockSampler(dev.index if dev.index is not None else 0) as clk:
         best_ts, tune = plan.tune(y, K, rel_tol=1e-6)
         fast_ms = timed("fast", -1, max(10, args.steps // 4), args.warmup)
         conv_ms = timed("conv", -1, max(10, args.steps // 4), args.warmup)
+        # the tuner times back to back; under this benchmark's protocol (L2
+        # flushed before every step) the hybrid at its point is checked
+        # against the hybrid at K (kernel sums throughout, the fast path
+        # timed just above) and the faster one is the headline switch point
+        tuned_ts = best_ts
+        probe_ms = timed("hybrid", tuned_ts, max(10, args.steps // 4), args.warmup)
+        if statistics.median(fast_ms) < statistics.median(probe_ms):
+            best_ts = K
+        ts_check = {"tuned": tuned_ts, "hybrid_at_tuned_ms_p50": statistics.median(probe_ms),
+                    "hybrid_at_K_ms_p50": statistics.median(fast_ms), "used": best_ts}
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        hyb_ms = timed("hybrid", -1, args.steps, args.warmup)
+        hyb_ms = timed("hybrid", best_ts, args.steps, args.warmup)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -732,7 +742,7 @@ def run_gpu(args, rank: int, world: int, refs=None):
 
     def e2e_step():
         y_dev.copy_(y_host, non_blocking=True)
-        plan.omp_into(y_dev, K, x, supp, iters, rn, rel_tol=1e-6, path="hybrid", t_switch=-1)
+        plan.omp_into(y_dev, K, x, supp, iters, rn, rel_tol=1e-6, path="hybrid", t_switch=best_ts)
         for h, d in zip(outs_host, (x, supp, iters, rn)):
             h.copy_(d, non_blocking=True)
 
@@ -754,7 +764,7 @@ def run_gpu(args, rank: int, world: int, refs=None):
 
     acc = None
     if rank == 0 and refs is not None and refs.get("config2") is not None:
-        step("hybrid", -1)
+        step("hybrid", best_ts)
         acc = accuracy_batch(plan, inst, y, (x, supp, iters, rn), refs["config2"], best_ts)
     extra = secondary(args, dev, plan, inst, stream, flush, refs) if (rank == 0 and not args.no_extra) else {}
 
@@ -784,7 +794,7 @@ def run_gpu(args, rank: int, world: int, refs=None):
         "value": solves, "ms_per_step": total_ms / args.steps,
         "p50_ms": statistics.median(hs), "p99_ms": hs[min(len(hs) - 1, int(0.99 * len(hs)))],
         "correlations_per_s": corr, "plan_ms": plan_ms, "t_switch": best_ts, "t_switch_default": default_ts,
-        "t_switch_sweep_ms": {str(k): round(v, 4) for k, v in tune.items()},
+        "t_switch_sweep_ms": {str(k): round(v, 4) for k, v in tune.items()}, "t_switch_check": ts_check,
         "fast": {"solves_per_s": B * world / (fast_med * 1e-3), "ms_per_step_p50": fast_med,
                  "frac_of_fp32_peak": correlation_flops(N, it_np, best_ts, "fast") / (fast_med * 1e-3) / 1e12
                  / fp32_measured},
@@ -880,7 +890,7 @@ def main():
                 "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "correlations_per_s": r["correlations_per_s"],
                 "fast": r["fast"], "conv": r["conv"], "plan_ms": r["plan_ms"],
                 "t_switch_default": r["t_switch_default"], "t_switch_sweep_ms": r["t_switch_sweep_ms"],
-                "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "accuracy": r["accuracy"],
+                "t_switch_check": r["t_switch_check"], "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "accuracy": r["accuracy"],
                 "clocks": r["clocks"],
                 "gpu_launches": r["gpu_launches"], "secondary": r["extra"]}
         print(json.dumps(line))
