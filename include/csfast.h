@@ -304,6 +304,12 @@ cs_status cs_omp_batched_tune(const cs_plan_t* plans, int64_t count, const void*
  * FP32 rounding) in at most 2m iterations for m columns (64 to 4000); a
  * column set whose columns are dependent is then solved only as far as
  * the iterations reach, instead of dropping the dependent column.
+ * On large plans the iterations after the first run in a device-side loop
+ * (a CUDA graph with a conditional while node, built per call, that ends as
+ * soon as every instance is finished) when at least 64 of them remain
+ * allowed (max_iter - 1 >= 64) and the stream is not being captured;
+ * otherwise the call queues max_iter iterations, those after an instance's
+ * end returning at once.
  * Limits: 1 <= K, 2K <= M (SP), 3K <= M (CoSaMP), K <= 128 for N <= 8192,
  * K <= 1024 for larger N. */
 cs_status cs_sp(cs_plan_t plan, const void* y_dev, int64_t batch, int32_t K, const cs_halt* halt,

@@ -2399,7 +2399,10 @@ cudaError_t lp_t(const PlanView& Pv, const PursuitLaunch& q, void* ws, cudaStrea
   // graph is not worth it or cannot be built
   if (q.max_iter < 1) return cudaSuccess;
   if ((e = iteration(s)) != cudaSuccess) return e;
-  if (q.max_iter - 1 >= kDeviceLoopMin) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+  // (a stream under capture gets the iterations queued into its graph)
+  if (q.max_iter - 1 >= kDeviceLoopMin && cap == cudaStreamCaptureStatusNone) {
     e = device_loop(s, a.ndone + 1, a.ndone, batch, q.max_iter - 1, iteration);
     if (e != cudaErrorNotSupported) return e;
     (void)cudaGetLastError();

@@ -132,3 +132,28 @@ def test_cg_dependent_columns_end(N, M):
     assert np.isfinite(x.cpu().numpy()).all() and np.isfinite(float(rn[0]))
     assert 1 <= int(it[0]) <= 6
     assert plan.device_error() == 0
+
+
+def test_pursuit_into_a_captured_graph():
+    """SP on a large plan with K = 96 (97 iterations allowed: eligible for
+    the device-side loop) called while the stream is being captured: the
+    iterations go into the caller's graph instead, and replaying it gives
+    the eager call's results bit for bit."""
+    N, M, K = 1 << 14, 2048, 96
+    inst = synth.make_batch("dft", N, M, K, 2, snr_db=None, prec="fp32", seed=31)
+    plan = binding.Plan(N, inst["omega"], "dft", "fp32")
+    y = torch.from_numpy(inst["Y"]).cuda()
+    x0, s0, i0, r0 = plan.pursuit("sp", y, K)  # eager: also grows the plan's workspace
+    torch.cuda.synchronize()
+    x = torch.zeros_like(x0)
+    s = torch.zeros_like(s0)
+    it = torch.zeros_like(i0)
+    rn = torch.zeros_like(r0)
+    st = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st, capture_error_mode="relaxed"):
+        plan.pursuit_into("sp", y, K, x, s, it, rn, stream=st)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(s, s0) and torch.equal(x, x0) and torch.equal(it, i0) and torch.equal(rn, r0)
+    assert plan.device_error() == 0
