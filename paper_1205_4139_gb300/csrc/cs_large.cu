@@ -1037,7 +1037,7 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 // memory carve-out of two CTAs per SM instead of three, which leaves the L1
 // cache room for the twiddle tables every element reads (measured at
 // N = 2^22: h_0 125 -> 115 us, an OMP iteration by transforms 5 % faster);
-// smaller tiles keep the driver's default.  The attribute is set only when it changes,
+// smaller tiles keep the CUDA default.  The attribute is set only when it changes,
 // so calls captured into a device-side loop make no runtime call.
 template <class K>
 cudaError_t pass_carveout(K kernel, size_t smem) {

@@ -237,7 +237,7 @@ extern "C" cs_status cs_server_create(int32_t workers, int64_t hbm_budget_bytes,
   S->budget = hbm_budget_bytes;
   S->t0 = std::chrono::steady_clock::now();
   // Keep up to the budget of freed job memory in the device's stream-ordered
-  // pool instead of returning it to the driver at every synchronisation, so
+  // pool instead of returning it to the CUDA driver at every synchronisation, so
   // that admitting a job reuses memory rather than allocating it anew.
   cudaMemPool_t pool = nullptr;
   if (cudaDeviceGetDefaultMemPool(&pool, S->device) == cudaSuccess) {
