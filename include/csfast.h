@@ -290,8 +290,11 @@ cs_status cs_omp_batched_tune(const cs_plan_t* plans, int64_t count, const void*
  * top_k breaks ties toward the lower index.  halt->path selects the
  * correlation: CS_PATH_FAST = kernel sums over the estimate's support
  * (Eq. kernelsum), CS_PATH_CONV = transforms, CS_PATH_HYBRID = kernel sums
- * when K <= t_switch.  Least squares are FP64 (normal equations, Cholesky
- * factor from c).  Outputs per instance: x_dev FP64 [K] and supp_dev [K] on
+ * when K <= t_switch.  Least squares are FP64 (normal equations with the
+ * Gram entries read off c): a Cholesky factor built column by column for
+ * column sets of at most 96, conjugate gradients above (one CTA per instance
+ * for N <= 8192, a cluster of 4 to 16 CTAs for larger N; see below).
+ * Outputs per instance: x_dev FP64 [K] and supp_dev [K] on
  * the final support in ascending column order (-1 / 0 past its size),
  * iters_dev (iterations run), resnorm_dev (||r|| / ||y||).
  * Large plans (N > 8192) run the same steps with the correlation over the
