@@ -130,7 +130,7 @@ cs_status cs_plan_create_ex(int64_t N, const int32_t* omega_host, int64_t M, int
                             uint32_t flags, void* stream, cs_plan_t* out);
 
 /* Device bytes held by the plan's tables (slot maps, Omega grouped by
- * transform row for N > 8192, c in its storage format, twiddles, status
+ * four-step row and by column for N > 8192, c in its storage format, twiddles, status
  * word), not counting the workspace or the chain twiddles shared by all
  * plans of one N. */
 cs_status cs_plan_memory(cs_plan_t plan, int64_t* table_bytes);
