@@ -35,3 +35,25 @@ def max_over_ranks(values, device=None) -> list[float]:
     t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return t.tolist()
+
+
+def argmax_over_ranks(value: float, index: int, device=None) -> tuple[float, int]:
+    """Identification across ranks that each hold a slice of the output index
+    j (one instance sharded by j): every rank passes its slice's largest
+    |h(j)|^2 and the lowest j that reaches it (-1 and a negative value when
+    its slice has no candidate); every rank gets the overall largest value
+    and the lowest j among the ranks that reach it (Algorithm 1.1 step 3 with
+    the ties to the lower index).  Two small all-reduces: MAX of the values,
+    then MIN of the indices of the ranks at that value."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value), int(index)
+    v = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    best = float(v.item())
+    big = 2 ** 62
+    j = torch.tensor([int(index) if (index >= 0 and float(value) == best) else big], dtype=torch.int64, device=device)
+    dist.all_reduce(j, op=dist.ReduceOp.MIN)
+    jj = int(j.item())
+    return best, (-1 if jj == big else jj)

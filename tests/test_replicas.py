@@ -58,6 +58,45 @@ def test_replica_split_two_gloo_ranks(tmp_path):
         assert g["red"] == [20.0, 5.0]  # the slowest rank's value in each slot
 
 
+def _argmax_rank(rank, port, out_dir, hs):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=WORLD)
+    try:
+        res = []
+        for h in hs:
+            n = len(h) // WORLD
+            sl = h[rank * n:(rank + 1) * n]
+            a = np.abs(sl) ** 2
+            loc = int(np.flatnonzero(a == a.max())[0])  # lowest j at the slice's maximum
+            res.append(replicas.argmax_over_ranks(float(a.max()), rank * n + loc))
+        gathered = [None] * WORLD
+        dist.all_gather_object(gathered, res)
+        if rank == 0:
+            torch.save(gathered, os.path.join(out_dir, "argmax.pt"))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_argmax_over_two_gloo_ranks(tmp_path):
+    """One instance sharded by output index over two ranks: the exchanged
+    arg-max equals the arg-max of the whole vector, with ties to the lower
+    index across the ranks' slices."""
+    rng = np.random.default_rng(3)
+    h1 = rng.standard_normal(64) + 1j * rng.standard_normal(64)
+    h2 = np.zeros(64)
+    h2[[7, 40]] = 2.0          # equal maxima in both slices: j = 7 wins
+    h3 = np.zeros(64)
+    h3[[45, 50]] = -3.0        # both in rank 1's slice: j = 45
+    hs = [h1, h2, h3]
+    tmp.spawn(_argmax_rank, args=(_free_port(), str(tmp_path), hs), nprocs=WORLD, join=True)
+    gathered = torch.load(os.path.join(tmp_path, "argmax.pt"), weights_only=False)
+    for h, got0, got1 in zip(hs, gathered[0], gathered[1]):
+        a = np.abs(h) ** 2
+        want = int(np.flatnonzero(a == a.max())[0])
+        assert got0 == got1 and got0[1] == want and got0[0] == a.max()
+
+
 def test_shard_host_rules():
     assert list(replicas.shard(1, 4, 5)) == [5, 6, 7, 8, 9]
     assert replicas.shard_seed(2, 1024) == 2048
