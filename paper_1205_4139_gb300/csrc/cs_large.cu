@@ -2187,12 +2187,18 @@ cudaError_t lq_cg_launch(const LPArgs<E>& a, int64_t batch, cudaStream_t s, bool
   auto kern = lq_cg_kernel<E, G>;
   cudaError_t e = allow_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  // set once per process (the launches inside a device-side loop are
+  // set once per device (the launches inside a device-side loop are
   // captured into a graph after the first iteration has set it)
-  static std::atomic<bool> nonportable{false};
-  if (G > 8 && !nonportable.load()) {
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
-    nonportable.store(true);
+  static std::atomic<unsigned long long> nonportable{0ull};  // one bit per device
+  if (G > 8) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(nonportable.load() & bit)) {
+      if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+        return e;
+      nonportable.fetch_or(bit);
+    }
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(batch * G));
